@@ -1,0 +1,304 @@
+"""Benchmark: shot-gradient evaluations per second on one GB300.
+
+One step = one full gradient evaluation of one shot (forward RK4 sweep with
+receiver sampling, misfit, reversed-time adjoint sweep, FP64 gradient time
+integrals) on the 64x64x32-element interior + 10-element PML mesh (2.43 M
+nodes, 2000 RK4 steps, 32x32 surface receivers, smooth Gaussian-random-field
+medium), with inputs resident in HBM. The e2e figure repeats the step through
+the C ABI with host buffers (material and observed traces uploaded, gradients
+downloaded every step).
+
+Multi-GPU: shots are independent, so each rank evaluates its own shot with no
+collective (weak scaling); the value is the sum over ranks.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import fwi_inputs as fi  # noqa: E402
+
+METRIC = "shot-gradient evals/s (element-stage updates/s), HBM roofline %, misfit drop/sec"
+UNIT = "shot-gradient evals/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    return fi.grf_64x64x32()
+
+
+def stage_bytes_per_step(ctx, nmat):
+    """Algorithmic HBM bytes of the four stage kernels of one RK4 step: each stage reads
+    its input state and writes its output once (13 floats per state variable per step:
+    2 + 3 + 3 + 5), 27 variables on PML nodes, 6 elsewhere, plus lambda and mu per stage."""
+    p = ctx.npml_nodes
+    n = ctx.nnode
+    return 13 * 4 * (27 * p + 6 * (n - p)) + 4 * 8 * nmat
+
+
+def setup(w, torch, dev):
+    from paper_1504_08340_gb300 import Context
+
+    ctx = Context(w.nx, w.ny, w.nz, w.npml, w.h, w.dt, w.nsteps, rho=w.rho)
+    lt, mt = (np.ascontiguousarray(a, dtype=np.float32) for a in fi.medium(w, "true"))
+    l0, m0 = (np.ascontiguousarray(a, dtype=np.float32) for a in fi.medium(w, "trial"))
+    ctx.set_sources(w.sources(), w.source_dirs(), "ricker", w.ricker())
+    ctx.set_receivers(w.receivers())
+    ctx.set_material(lt, mt)
+    obs = torch.zeros(ctx.trace_shape(1), dtype=torch.float32, device=dev)
+    ctx.forward(out=obs)  # observed data: the true medium's response (outside the timed region)
+    ctx.set_material(torch.tensor(l0, device=dev), torch.tensor(m0, device=dev))
+    return ctx, obs, (l0, m0)
+
+
+def cpu_baseline(w, steps_sample=2, repeats=1):
+    """The oracle, as it stands, on a bounded sample: `steps_sample` forward and adjoint RK4
+    steps of the full-size mesh, scaled to one full gradient evaluation."""
+    import oracle
+
+    o = oracle.Oracle(w.nx, w.ny, w.nz, w.npml, h=w.h, rho=w.rho)
+    l0, m0 = fi.medium(w, "trial")
+    o.set_material(l0, m0)
+    src = [o.node_id(*s) for s in w.sources()]
+    rec = [o.node_id(*r) for r in w.receivers()]
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        tr, hist = o.forward(w.dt, steps_sample, src, w.source_dirs(), "ricker", (w.f0, 0.0, w.amp), rec,
+                             keep_history=True)
+        o.adjoint_gradient(w.dt, steps_sample, rec, tr, hist)
+        t = time.perf_counter() - t0
+        best = t if best is None else min(best, t)
+    per_eval = best * (w.nsteps / steps_sample)
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": o.threads, "kind": "oracle",
+            "sample": f"{steps_sample} forward + {steps_sample} adjoint RK4 steps of the {w.name} mesh "
+                      f"(of {w.nsteps} each), FP64 C oracle, {o.threads} threads, scaled x{w.nsteps / steps_sample:g}",
+            "sample_seconds": best}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_baseline(w, steps_sample=1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, steps_sample=1)["value"])
+    total = time.perf_counter() - t0
+    cb = cpu_baseline.__defaults__  # noqa: F841
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "mesh": f"{w.nx}x{w.ny}x{w.nz}+{w.npml} PML", "nsteps": w.nsteps,
+                       "receivers": w.nrec_side ** 2, "shots_per_step": 1},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(),
+                             "sample": f"each step: 1 forward + 1 adjoint RK4 step of {w.name} "
+                                       f"(of {w.nsteps}), scaled x{w.nsteps}; wall {total:.1f} s for {args.steps} steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = workload()
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx, obs, (l0, m0) = setup(w, torch, dev)
+    gl = torch.empty(ctx.mat_shape(), dtype=torch.float64, device=dev)
+    gm = torch.empty_like(gl)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        J, _, _ = ctx.adjoint_gradient(obs, g_lambda=gl, g_mu=gm)
+    ctx.reset_timing()
+    ctx.set_timing(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J, _, _ = ctx.adjoint_gradient(obs, g_lambda=gl, g_mu=gm)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ctx.set_timing(False)
+    stage_ms, stage_launches = ctx.timing(0)
+    grad_ms, grad_launches = ctx.timing(1)
+    _, all_launches = ctx.timing(3)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world / (ms_max / 1e3)
+
+    hbm, peak_kind = _peaks()
+    bytes_step = stage_bytes_per_step(ctx, ctx.nmat)
+    total_stage_bytes = bytes_step / 4.0 * stage_launches
+    achieved = total_stage_bytes / (stage_ms / 1e3) / 1e9 if stage_ms > 0 else None
+    elem_stage = ctx.nelem * 4 * w.nsteps * 2  # forward + adjoint sweeps
+
+    e2e = None
+    if not args.no_e2e:
+        obs_h = torch.empty(ctx.trace_shape(1), dtype=torch.float32, pin_memory=True)
+        obs_h.copy_(obs.cpu())
+        lam_h = torch.tensor(l0).pin_memory()
+        mu_h = torch.tensor(m0).pin_memory()
+        gl_h = torch.empty(ctx.mat_shape(), dtype=torch.float64, pin_memory=True)
+        gm_h = torch.empty_like(gl_h).pin_memory()
+        on, mn, gln, gmn = obs_h.numpy(), lam_h.numpy(), gl_h.numpy(), gm_h.numpy()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_material(mn, mu_h.numpy())
+            Je, _, _ = ctx.adjoint_gradient(on, g_lambda=gln, g_mu=gmn)
+        barrier()
+        te = (time.perf_counter() - t0) / args.steps
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(on.nbytes + mn.nbytes + mu_h.numpy().nbytes),
+               "d2h_bytes_per_step": int(gln.nbytes + gmn.nbytes + 8)}
+        assert abs(Je - J) <= 1e-12 * abs(J)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "mesh": f"{w.nx}x{w.ny}x{w.nz}+{w.npml} PML, h={w.h} m",
+                       "nodes": ctx.nnode, "elements": ctx.nelem, "nsteps": w.nsteps, "dt": w.dt,
+                       "receivers": w.nrec_side ** 2, "shots_per_step_per_gpu": 1,
+                       "parallelism": f"shot replicas x{world}",
+                       "l2": "inputs larger than L2 (1 GB state, 26 GB history per step)"},
+            "element_stage_updates_per_s": value * elem_stage,
+            "misfit": J,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                         "kernel": "stage_kernel (fused RK4 stage)", "peak_kind": peak_kind,
+                         "bytes_per_launch": bytes_step / 4.0,
+                         "avg_launch_ms": stage_ms / max(stage_launches, 1),
+                         "stage_share_of_step": stage_ms / (ms * args.steps) if ms > 0 else None},
+            "gradient_kernel_ms_per_step": grad_ms / args.steps,
+            "gpu_launches": int(all_launches),
+            "clocks": clocks,
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * fwi.h -- C ABI of the GB300 per-shot material-gradient library for
+ * time-domain elastic full-waveform inversion in PML-truncated 3D media
+ * (Fathi, Kallivokas & Poursartip, arXiv:1504.08340).
+ *
+ * The library evaluates, for a trial distribution of the Lame parameters
+ * lambda(x), mu(x), the misfit (7) between computed and observed receiver
+ * displacements and its gradients dJ/dlambda_i, dJ/dmu_i (the misfit parts
+ * g_mis of (18), Appendix C (C.1f)/(C.1g)). One evaluation runs
+ *   - the state problem: the semi-discrete system (5) of the hybrid
+ *     spectral-element discretisation (displacement-only interior, displacement-
+ *     stress PML, 27-node LGL hexahedra) as the first-order system (6),
+ *     integrated by classic RK4 (Sec. 2);
+ *   - the adjoint problem (14)/(15) with the transposed system matrices,
+ *     integrated by the reverse RK4 of Appendix B, driven by the receiver
+ *     residuals (13a);
+ *   - the time integrals (C.1f)/(C.1g) over the interior domain, in FP64.
+ * All wavefield arithmetic runs in CUDA kernels on the GPU of the context's
+ * stream, in FP32 with FP64 accumulation of J and of the gradients.
+ *
+ * Mesh. A structured box of 27-node hexahedra of edge h: nx*ny*nz interior
+ * ("regular domain") elements, wrapped by npml PML elements on the faces
+ * x-, x+, y-, y+ and the bottom (and the top when top_pml = 1; the paper's
+ * configuration, top_pml = 0, has a traction-free ground surface, Eq. (2a)).
+ * Nodes are indexed (i, j, k), 0 <= i <= 2(nx + 2 npml), 0 <= j <= 2(ny + 2 npml),
+ * 0 <= k <= 2(nz + npml [+ npml]), i along x, j along y, k along depth, k = 0 at
+ * the top. Node number n = (k * NJ + j) * NI + i with NI, NJ the node counts
+ * along x and y. Displacements vanish on the outer PML faces (2c).
+ *
+ * Material. lambda and mu are nodal (quadratic) on the interior nodes only,
+ * FP32 arrays of (2nz+1)(2ny+1)(2nx+1) values ordered [k][j][i] (i fastest),
+ * in Pa; they are extended into the PML by the value at the nearest interface
+ * node (Sec. 4.1: "extended into the PML"). rho is constant.
+ *
+ * Conventions for every call:
+ *   - the caller owns every array it passes; the library keeps no caller
+ *     pointer beyond the call;
+ *   - on_device = 1: the array arguments marked "host or device" are device
+ *     pointers usable on the context's stream; on_device = 0: host pointers;
+ *   - every call returns an fwi_status; fwi_last_error() gives detail;
+ *   - on an error the outputs are left untouched; the context stays usable
+ *     except after FWI_E_CUDA, which is sticky;
+ *   - calls are synchronous with respect to their outputs: they wait for the
+ *     context's stream before returning.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fwi_ctx fwi_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  FWI_OK = 0,
+  FWI_E_INVAL = 1,     /* invalid argument or size */
+  FWI_E_NOMEM = 2,     /* device or host allocation failed */
+  FWI_E_CUDA = 3,      /* a CUDA call failed; sticky */
+  FWI_E_UNSTABLE = 4,  /* time step above the RK4 stability estimate */
+  FWI_E_NONFINITE = 5, /* NaN or Inf in material, traces or gradients */
+  FWI_E_TIMEOUT = 6,   /* a bounded device wait gave up */
+  FWI_E_STATE = 7      /* call out of order (e.g. no material or receivers yet) */
+} fwi_status;
+
+enum { FWI_WAVELET_RICKER = 0, FWI_WAVELET_GAUSS = 1 };
+
+typedef struct {
+  int nx, ny, nz;   /* interior elements per axis (>= 1) */
+  int npml;         /* PML elements on each truncated face (>= 0) */
+  int top_pml;      /* 0: free ground surface (paper); 1: PML on the top face too */
+  double h;         /* element edge, m */
+  double rho;       /* mass density, kg/m^3 */
+  double pml_alpha0;/* PML stretch amplitude alpha_o (Sec. 4.1 uses 5) */
+  double pml_beta0; /* PML attenuation amplitude beta_o, 1/s (Sec. 4.1 uses 400) */
+  int pml_m;        /* PML profile exponent m (Sec. 4.1 uses 2) */
+  double dt;        /* RK4 step, s */
+  int nsteps;       /* number of steps; traces have nsteps + 1 samples t_n = n dt */
+  void *cuda_stream;/* cudaStream_t for all work, or NULL for the legacy default stream */
+} fwi_config;
+
+/* Create a context for one mesh (Sec. 2 / Fig. 3 domain layout). Allocates the
+ * device state (four RK4 stage buffers of 27 FP32 fields per node) on the
+ * current CUDA device. Errors: FWI_E_INVAL (sizes), FWI_E_NOMEM, FWI_E_CUDA. */
+fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out);
+
+/* Release the context and all its device memory. NULL is accepted. */
+void fwi_destroy(fwi_ctx *ctx);
+
+/* Last error message of this context (never NULL; "" when none). */
+const char *fwi_last_error(const fwi_ctx *ctx);
+
+/* Static description of a status code. */
+const char *fwi_status_string(fwi_status s);
+
+/* Sizes: dims[0..2] nodes per axis (NI, NJ, NK), dims[3] node count,
+ * dims[4] interior (material) node count, dims[5] field stride in floats of the
+ * state layout used by fwi_rhs, dims[6] number of elements, dims[7] number of
+ * PML nodes. */
+fwi_status fwi_get_dims(const fwi_ctx *ctx, int64_t dims[8]);
+
+/* Set the trial Lame parameters (D4: nodal values on the interior nodes,
+ * [k][j][i], Pa; host or device). Checks finiteness, mu > 0, lambda + 2 mu > 0
+ * (FWI_E_NONFINITE / FWI_E_INVAL) and the RK4 time-step limit estimated as
+ * dt * vp_max / (h/2) <= 0.66 (FWI_E_UNSTABLE). */
+fwi_status fwi_set_material(fwi_ctx *ctx, const float *lambda, const float *mu, int on_device);
+
+/* Point-load sources (the right side of (3a) for a nodal load): shot s loads
+ * node node_ijk[3s..3s+2] (host) with force dir[3s..3s+2] * r(t) (host), where
+ * r is the wavelet: FWI_WAVELET_RICKER, wparams = {f0 [Hz], t0 [s], amplitude [N]},
+ * r = A (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2);
+ * FWI_WAVELET_GAUSS (Table 1 pulse, read as A exp(-(t - mu)^2 / sigma)),
+ * wparams = {mu [s], sigma [s^2], amplitude [N]}. The node must not lie on a
+ * Dirichlet face. Errors: FWI_E_INVAL. */
+fwi_status fwi_set_sources(fwi_ctx *ctx, int nshots, const int *node_ijk, const double *dir,
+                           int wavelet, const double *wparams);
+
+/* Receivers (delta(x - x_j) of (7)): nrec distinct nodes node_ijk[3r..3r+2]
+ * (host), not on a Dirichlet face. Errors: FWI_E_INVAL. */
+fwi_status fwi_set_receivers(fwi_ctx *ctx, int nrec, const int *node_ijk);
+
+/* State problem (6) for shots shot0 .. shot0+nshots-1; writes the receiver
+ * displacements traces[s][n][r][c] = u_c(x_r, t_n), n = 0..nsteps, FP32
+ * (host or device, caller-owned, nshots*(nsteps+1)*nrec*3 floats).
+ * Errors: FWI_E_STATE (no material / sources / receivers), FWI_E_INVAL,
+ * FWI_E_NONFINITE, FWI_E_CUDA. */
+fwi_status fwi_forward(fwi_ctx *ctx, int shot0, int nshots, float *traces, int on_device);
+
+/* Misfit (7) without regularisation, summed over the shots, with the trapezoid
+ * rule in time: J = 1/2 sum_s sum_r sum_n w_n dt |u - u_m|^2 (w_0 = w_N = 1/2).
+ * observed: same layout as fwi_forward's traces (host or device). *J: host. */
+fwi_status fwi_misfit(fwi_ctx *ctx, int shot0, int nshots, const float *observed, int on_device,
+                      double *J);
+
+/* Misfit and its gradients for shots shot0 .. shot0+nshots-1 (Algorithm 2,
+ * lines 6-8): state solve (6), adjoint solve (15)/Appendix B, and
+ *   g_lambda[i] = -int_0^T int_RD chi_i (div w)(div u)            (C.1f)
+ *   g_mu[i]     = -int_0^T int_RD chi_i 2 eps(w):eps(u)           (C.1g)
+ * i.e. g_mis = dJ/dlambda_i, dJ/dmu_i on the interior nodes ([k][j][i], FP64,
+ * summed over the shots; host or device per on_device). The full gradient of
+ * (18) with R = 0 is g = Mtilde^-1 g_mis, see fwi_get_mass_tilde. *J: host.
+ * Device memory for the forward displacement history, nsteps+1 copies of the
+ * interior displacement field (12 bytes per interior node per step), is
+ * allocated on the first call and kept. Errors as fwi_forward. */
+fwi_status fwi_adjoint_gradient(fwi_ctx *ctx, int shot0, int nshots, const float *observed,
+                                int on_device, double *J, double *g_lambda, double *g_mu);
+
+/* Diagonal of the lumped mass-like matrix Mtilde of (C.1a), FP64, on the
+ * interior nodes (host array of dims[4] values). */
+fwi_status fwi_get_mass_tilde(fwi_ctx *ctx, double *mtilde);
+
+/* Right side of the first-order system at one state (no loads):
+ * adjoint = 0: Eq. (6), rate = (x1|PML, x2, M^-1(-G x0 - K x1 - C x2));
+ * adjoint = 1: the adjoint system in reversed time s = T - t,
+ *   M z'' + C' z' + K' z + G' zbar = 0 with C' = D C^T D, K' = D K^T D,
+ *   G' = D G^T D, D = diag(I on displacements, -I on stresses); with
+ *   z = D y1(T - s), z' = -D y2(T - s), zbar = -D y0(T - s) this is (15).
+ * state and rate: 27 fields of dims[5] floats each (host or device); field
+ * 9*l + c holds level l (0: history, 1: value, 2: rate) and component c
+ * (0..2 displacement x,y,z; 3..8 stress xx,yy,zz,yz,xz,xy) of every node.
+ * Displacement fields must be zero on the Dirichlet faces and history / stress
+ * fields zero off the PML nodes. Errors: FWI_E_STATE (no material). */
+fwi_status fwi_rhs(fwi_ctx *ctx, int adjoint, const float *state, float *rate, int on_device);
+
+/* Kernel timing: with enable = 1 every stage-kernel launch of later calls is
+ * bracketed by CUDA events on the context's stream; fwi_get_timing returns the
+ * summed device time (ms) and launch count of kernel class `which`
+ * (0: RK stage kernels, 1: gradient kernel, 2: point-load / sampling kernels,
+ * 3: all kernels launched, time unset) since the last reset. */
+fwi_status fwi_set_timing(fwi_ctx *ctx, int enable);
+fwi_status fwi_get_timing(fwi_ctx *ctx, int which, double *ms, int64_t *launches);
+fwi_status fwi_reset_timing(fwi_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWI_H */

@@ -1,0 +1,797 @@
+// fwi_api.cu -- host side of the C ABI declared in include/fwi.h.
+//
+// The host code validates arguments, owns the device buffers, builds the
+// small per-axis tables (PML stretch functions, wavelet samples, lumped-mass
+// inverses at the loaded nodes) in FP64 and drives the time loops; every step
+// of the wavefield, misfit and gradient arithmetic runs in the kernels of
+// fwi_kernels.cu on the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fwi.h"
+#include "fwi_internal.h"
+
+struct fwi_ctx {
+  fwi_config cfg{};
+  fwi::Geo geo{};
+  cudaStream_t stream = nullptr;
+  bool cuda_failed = false;
+  std::string err;
+  int64_t nelem = 0, npml_nodes = 0;
+
+  float *state[4] = {nullptr, nullptr, nullptr, nullptr};  // X, Y2, Y3, Y4
+  float *d_alpha[3] = {nullptr, nullptr, nullptr};
+  float *d_beta[3] = {nullptr, nullptr, nullptr};
+  std::vector<double> h_alpha[3], h_beta[3];
+  float *d_lam = nullptr, *d_mu = nullptr;
+  bool have_material = false;
+
+  int nshots = 0;
+  std::vector<int64_t> src_node;
+  std::vector<double> src_dir;
+  int wavelet = 0;
+  double wparams[3] = {0, 0, 0};
+  float *d_wave = nullptr;
+  int64_t *d_src_node = nullptr;
+  float *d_src_vec = nullptr;
+
+  int nrec = 0;
+  std::vector<int64_t> rec_node;
+  int64_t *d_rec_node = nullptr;
+  float *d_rec_vec = nullptr;
+
+  float *d_traces = nullptr, *d_obs = nullptr, *d_resid = nullptr;
+  double *d_part = nullptr, *d_J = nullptr;
+  int d_J_cap = 0;
+  int *d_flag = nullptr;
+  float *d_hist = nullptr;
+  double *d_gl = nullptr, *d_gm = nullptr;
+
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  std::vector<int> ev_class;
+  double t_ms[4] = {0, 0, 0, 0};
+  int64_t t_launch[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+fwi_status fail(fwi_ctx *c, fwi_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (s == FWI_E_CUDA) c->cuda_failed = true;
+  }
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                          \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess)                                                                           \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? FWI_E_NOMEM : FWI_E_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                                \
+  } while (0)
+
+#define TRY(expr)                     \
+  do {                                \
+    fwi_status s_ = (expr);           \
+    if (s_ != FWI_OK) return s_;      \
+  } while (0)
+
+template <class T>
+fwi_status dalloc(fwi_ctx *c, T **p, size_t n) {
+  if (*p) return FWI_OK;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, FWI_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+  }
+  return FWI_OK;
+}
+
+template <class T>
+void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+bool is_dirichlet(const fwi_ctx *c, int i, int j, int k) {
+  const int *n = c->geo.n;
+  return i == 0 || i == n[0] - 1 || j == 0 || j == n[1] - 1 || k == n[2] - 1 || (c->geo.top_dir && k == 0);
+}
+
+// number of elements containing node coordinate cc along axis ax
+int elems_along(const fwi_ctx *c, int ax, int cc) {
+  if (cc & 1) return 1;
+  return (cc >= 2) + (cc <= c->geo.n[ax] - 3);
+}
+
+// lumped u-row mass rho * a(x) * W * detJ * (elements around the node) -- (3a)
+double mass_u(const fwi_ctx *c, int i, int j, int k) {
+  const int cc[3] = {i, j, k};
+  double w = 1.0, nel = 1.0, a = 1.0, hh = 0.5 * c->cfg.h;
+  for (int ax = 0; ax < 3; ax++) {
+    w *= (cc[ax] & 1) ? 4.0 / 3.0 : 1.0 / 3.0;
+    nel *= elems_along(c, ax, cc[ax]);
+    a *= c->h_alpha[ax][cc[ax]];
+  }
+  return c->cfg.rho * a * w * hh * hh * hh * nel;
+}
+
+fwi_status check_stream(fwi_ctx *c) {
+  if (c->cuda_failed) return fail(c, FWI_E_CUDA, "context unusable after an earlier CUDA error: %s", c->err.c_str());
+  return FWI_OK;
+}
+
+// ---- timing of kernel classes
+void time_begin(fwi_ctx *c, cudaEvent_t *e0) {
+  *e0 = nullptr;
+  if (!c->timing) return;
+  if (c->ev_free.size() < 2) {
+    for (int i = 0; i < 256; i++) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      c->ev_free.push_back(e);
+    }
+  }
+  if (c->ev_free.empty()) return;
+  *e0 = c->ev_free.back();
+  c->ev_free.pop_back();
+  cudaEventRecord(*e0, c->stream);
+}
+
+void time_end(fwi_ctx *c, cudaEvent_t e0, int cls) {
+  c->t_launch[cls]++;
+  c->t_launch[3]++;
+  if (!c->timing || !e0) return;
+  if (c->ev_free.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->ev_free.push_back(e);
+  }
+  cudaEvent_t e1 = c->ev_free.back();
+  c->ev_free.pop_back();
+  cudaEventRecord(e1, c->stream);
+  c->ev_pending.push_back({e0, e1});
+  c->ev_class.push_back(cls);
+}
+
+fwi_status time_flush(fwi_ctx *c) {
+  if (c->ev_pending.empty()) return FWI_OK;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < c->ev_pending.size(); i++) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_pending[i].first, c->ev_pending[i].second);
+    c->t_ms[c->ev_class[i]] += ms;
+    c->ev_free.push_back(c->ev_pending[i].first);
+    c->ev_free.push_back(c->ev_pending[i].second);
+  }
+  c->ev_pending.clear();
+  c->ev_class.clear();
+  return FWI_OK;
+}
+
+fwi_status stage(fwi_ctx *c, bool adj, const fwi::StageArgs &a) {
+  cudaEvent_t e0;
+  time_begin(c, &e0);
+  fwi::launch_stage(c->geo, a, adj, c->stream);
+  time_end(c, e0, 0);
+  CUDA_TRY(c, cudaGetLastError());
+  if (c->ev_pending.size() > 400000) TRY(time_flush(c));
+  return FWI_OK;
+}
+
+fwi_status point(fwi_ctx *c, const fwi::PointArgs &p) {
+  fwi::launch_point(p, c->stream);
+  c->t_launch[2]++;
+  c->t_launch[3]++;
+  CUDA_TRY(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status zero_state(fwi_ctx *c) {
+  const size_t bytes = sizeof(float) * (size_t)fwi::kFields * c->geo.stride;
+  for (int b = 0; b < 4; b++) CUDA_TRY(c, cudaMemsetAsync(c->state[b], 0, bytes, c->stream));
+  return FWI_OK;
+}
+
+// One RK4 step (4 fused stage kernels) of the forward (adj = false) or the
+// reversed-time adjoint (adj = true) system, with the point loads of the step.
+fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot, float *hist_slot) {
+  const float dt = (float)c->cfg.dt;
+  float *X = c->state[0], *Y2 = c->state[1], *Y3 = c->state[2], *Y4 = c->state[3];
+  const float *ins[4] = {X, Y2, Y3, Y4};
+  float *outs[4] = {Y2, Y3, Y4, X};
+  const float cdt[4] = {0.5f * dt, 0.5f * dt, dt, dt / 6.0f};
+  const int N = c->cfg.nsteps;
+  for (int s = 0; s < 4; s++) {
+    fwi::StageArgs a{};
+    a.Y = ins[s];
+    a.X = X;
+    a.Y2 = Y2;
+    a.Y3 = Y3;
+    a.out = outs[s];
+    a.cdt = cdt[s];
+    a.stage = s + 1;
+    a.hist = (s == 3) ? hist_slot : nullptr;
+    TRY(stage(c, adj, a));
+    fwi::PointArgs p{};
+    p.buf = outs[s];
+    p.stride = c->geo.stride;
+    p.cdt = cdt[s];
+    if (!adj) {
+      // stage times t_n, t_n + dt/2, t_n + dt/2, t_n + dt; wavelet sampled every dt/2
+      p.mode = 0;
+      p.npts = 1;
+      p.node = c->d_src_node + shot;
+      p.vec = c->d_src_vec + 3 * shot;
+      p.table = c->d_wave;
+      p.i0 = (s == 0) ? 2 * n : (s == 3 ? 2 * n + 2 : 2 * n + 1);
+      p.i1 = -1;
+    } else {
+      // reversed time: s_m <-> t_{N-m}; half steps use the mean of the two samples
+      p.mode = 1;
+      p.npts = c->nrec;
+      p.node = c->d_rec_node;
+      p.vec = c->d_rec_vec;
+      p.table = c->d_resid;
+      p.i0 = (s == 3) ? N - n - 1 : N - n;
+      p.i1 = (s == 1 || s == 2) ? N - n - 1 : -1;
+    }
+    TRY(point(c, p));
+  }
+  return FWI_OK;
+}
+
+fwi_status require_ready(fwi_ctx *c, int shot0, int nshots) {
+  TRY(check_stream(c));
+  if (!c->have_material) return fail(c, FWI_E_STATE, "material not set");
+  if (c->nshots <= 0) return fail(c, FWI_E_STATE, "sources not set");
+  if (c->nrec <= 0) return fail(c, FWI_E_STATE, "receivers not set");
+  if (shot0 < 0 || nshots < 1 || shot0 + nshots > c->nshots)
+    return fail(c, FWI_E_INVAL, "shot range [%d, %d) outside [0, %d)", shot0, shot0 + nshots, c->nshots);
+  return FWI_OK;
+}
+
+fwi_status ensure_trace_buffers(fwi_ctx *c) {
+  const size_t nt = (size_t)(c->cfg.nsteps + 1) * c->nrec * 3;
+  TRY(dalloc(c, &c->d_traces, nt));
+  TRY(dalloc(c, &c->d_obs, nt));
+  TRY(dalloc(c, &c->d_resid, nt));
+  TRY(dalloc(c, &c->d_part, 1024));
+  TRY(dalloc(c, &c->d_flag, 4));
+  return FWI_OK;
+}
+
+// forward sweep of one shot into d_traces; hist: optional displacement history
+fwi_status forward_sweep(fwi_ctx *c, int shot, float *hist) {
+  TRY(zero_state(c));
+  const int64_t per_step = (int64_t)c->nrec * 3;
+  const size_t hstep = (size_t)3 * c->geo.nmat;
+  if (hist) CUDA_TRY(c, cudaMemsetAsync(hist, 0, sizeof(float) * hstep, c->stream));
+  fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces, c->stream);
+  for (int n = 0; n < c->cfg.nsteps; n++) {
+    TRY(rk4_step(c, false, n, shot, hist ? hist + (size_t)(n + 1) * hstep : nullptr));
+    fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces + (n + 1) * per_step,
+                       c->stream);
+    c->t_launch[2]++;
+    c->t_launch[3]++;
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+// residual and misfit of the traces in d_traces against observed (device) -> d_J[slot]
+fwi_status misfit_of_traces(fwi_ctx *c, const float *obs_dev, int slot) {
+  const int64_t per_step = (int64_t)c->nrec * 3;
+  const int64_t n = per_step * (c->cfg.nsteps + 1);
+  fwi::launch_residual(c->d_traces, obs_dev, c->d_resid, n, per_step, c->cfg.nsteps, c->cfg.dt, c->d_part,
+                       c->d_flag, c->stream);
+  fwi::launch_sum(c->d_part, fwi::misfit_blocks(n), c->d_J + slot, c->stream);
+  c->t_launch[3] += 2;
+  CUDA_TRY(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status ensure_J(fwi_ctx *c, int n) {
+  if (c->d_J_cap < n) {
+    dfree(c->d_J);
+    TRY(dalloc(c, &c->d_J, (size_t)n));
+    c->d_J_cap = n;
+  }
+  return FWI_OK;
+}
+
+const float *observed_for_shot(fwi_ctx *c, const float *observed, int on_device, int s, fwi_status *st) {
+  const size_t nt = (size_t)(c->cfg.nsteps + 1) * c->nrec * 3;
+  *st = FWI_OK;
+  if (on_device) return observed + (size_t)s * nt;
+  cudaError_t e = cudaMemcpyAsync(c->d_obs, observed + (size_t)s * nt, nt * sizeof(float), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e != cudaSuccess) {
+    *st = fail(c, FWI_E_CUDA, "observed upload: %s", cudaGetErrorString(e));
+    return nullptr;
+  }
+  return c->d_obs;
+}
+
+fwi_status finish_J(fwi_ctx *c, int nshots, double *J) {
+  std::vector<double> hJ(nshots);
+  int flag = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(hJ.data(), c->d_J, sizeof(double) * nshots, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (flag) return fail(c, FWI_E_NONFINITE, "non-finite value in the computed traces");
+  double s = 0.0;
+  for (int i = 0; i < nshots; i++) s += hJ[i];
+  if (!std::isfinite(s)) return fail(c, FWI_E_NONFINITE, "non-finite misfit");
+  if (J) *J = s;
+  return FWI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fwi_status_string(fwi_status s) {
+  switch (s) {
+    case FWI_OK: return "ok";
+    case FWI_E_INVAL: return "invalid argument";
+    case FWI_E_NOMEM: return "out of memory";
+    case FWI_E_CUDA: return "CUDA error";
+    case FWI_E_UNSTABLE: return "time step above the RK4 stability estimate";
+    case FWI_E_NONFINITE: return "non-finite value";
+    case FWI_E_TIMEOUT: return "bounded device wait gave up";
+    case FWI_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char *fwi_last_error(const fwi_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
+  if (!cfg || !out) return FWI_E_INVAL;
+  *out = nullptr;
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || cfg->npml < 0 || !(cfg->h > 0) || !(cfg->rho > 0) ||
+      !(cfg->dt > 0) || cfg->nsteps < 1 || cfg->pml_m < 0 || !(cfg->pml_alpha0 >= 0) || !(cfg->pml_beta0 >= 0))
+    return FWI_E_INVAL;
+  if (cfg->npml == 0 && cfg->top_pml) return FWI_E_INVAL;
+  const int64_t nI = 2LL * (cfg->nx + 2LL * cfg->npml) + 1, nJ = 2LL * (cfg->ny + 2LL * cfg->npml) + 1,
+                nK = 2LL * (cfg->nz + cfg->npml + (cfg->top_pml ? cfg->npml : 0)) + 1;
+  if (nI * nJ * nK > (1LL << 34)) return FWI_E_INVAL;
+  fwi_ctx *c = new (std::nothrow) fwi_ctx();
+  if (!c) return FWI_E_NOMEM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)cfg->cuda_stream;
+  fwi::Geo &g = c->geo;
+  g.n[0] = (int)nI;
+  g.n[1] = (int)nJ;
+  g.n[2] = (int)nK;
+  g.lo[0] = cfg->npml;
+  g.lo[1] = cfg->npml;
+  g.lo[2] = cfg->top_pml ? cfg->npml : 0;
+  g.hi[0] = g.lo[0] + cfg->nx;
+  g.hi[1] = g.lo[1] + cfg->ny;
+  g.hi[2] = g.lo[2] + cfg->nz;
+  g.m[0] = 2 * cfg->nx + 1;
+  g.m[1] = 2 * cfg->ny + 1;
+  g.m[2] = 2 * cfg->nz + 1;
+  g.top_dir = cfg->top_pml ? 1 : 0;
+  g.nnode = nI * nJ * nK;
+  g.nmat = (int64_t)g.m[0] * g.m[1] * g.m[2];
+  g.stride = (g.nnode + 63) / 64 * 64;
+  g.inv_h = (float)(1.0 / cfg->h);
+  g.rho = (float)cfg->rho;
+  g.wdetj = (float)(0.125 * cfg->h * cfg->h * cfg->h);
+  c->nelem = (int64_t)(nI / 2) * (nJ / 2) * (nK / 2);
+  {
+    // PML nodes: nodes of at least one PML element
+    int64_t rd_only = 1;
+    for (int ax = 0; ax < 3; ax++) {
+      // coordinates whose every element along this axis is interior
+      int64_t cnt = 0;
+      for (int cc = 0; cc < g.n[ax]; cc++) {
+        bool all = true;
+        if (cc & 1) {
+          int e = (cc - 1) / 2;
+          all = e >= g.lo[ax] && e < g.hi[ax];
+        } else {
+          if (cc >= 2) all = all && (cc / 2 - 1 >= g.lo[ax] && cc / 2 - 1 < g.hi[ax]);
+          if (cc <= g.n[ax] - 3) all = all && (cc / 2 >= g.lo[ax] && cc / 2 < g.hi[ax]);
+        }
+        cnt += all;
+      }
+      rd_only *= cnt;
+    }
+    c->npml_nodes = g.nnode - rd_only;
+  }
+  // PML stretch functions per axis, FP64 on the host (reading of [13]):
+  // alpha = 1 + alpha0 (l/L)^m, beta = beta0 (l/L)^m, l = depth into the layer
+  const double L = cfg->npml * cfg->h;
+  for (int ax = 0; ax < 3; ax++) {
+    c->h_alpha[ax].resize(g.n[ax]);
+    c->h_beta[ax].resize(g.n[ax]);
+    const int a0 = 2 * g.lo[ax], b0 = 2 * g.hi[ax];
+    for (int cc = 0; cc < g.n[ax]; cc++) {
+      double l = cc < a0 ? (a0 - cc) * 0.5 * cfg->h : (cc > b0 ? (cc - b0) * 0.5 * cfg->h : 0.0);
+      double r = (L > 0 && l > 0) ? std::pow(l / L, (double)cfg->pml_m) : 0.0;
+      c->h_alpha[ax][cc] = 1.0 + cfg->pml_alpha0 * r;
+      c->h_beta[ax][cc] = cfg->pml_beta0 * r;
+    }
+  }
+  fwi_status st = FWI_OK;
+  const size_t sbytes = (size_t)fwi::kFields * g.stride;
+  for (int b = 0; b < 4 && st == FWI_OK; b++) st = dalloc(c, &c->state[b], sbytes);
+  for (int ax = 0; ax < 3 && st == FWI_OK; ax++) {
+    st = dalloc(c, &c->d_alpha[ax], g.n[ax]);
+    if (st == FWI_OK) st = dalloc(c, &c->d_beta[ax], g.n[ax]);
+    if (st != FWI_OK) break;
+    std::vector<float> fa(g.n[ax]), fb(g.n[ax]);
+    for (int i = 0; i < g.n[ax]; i++) {
+      fa[i] = (float)c->h_alpha[ax][i];
+      fb[i] = (float)c->h_beta[ax][i];
+    }
+    if (cudaMemcpy(c->d_alpha[ax], fa.data(), sizeof(float) * g.n[ax], cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_beta[ax], fb.data(), sizeof(float) * g.n[ax], cudaMemcpyHostToDevice) != cudaSuccess)
+      st = fail(c, FWI_E_CUDA, "stretch table upload failed");
+    g.alpha[ax] = c->d_alpha[ax];
+    g.beta[ax] = c->d_beta[ax];
+  }
+  if (st == FWI_OK) st = dalloc(c, &c->d_lam, (size_t)g.nmat);
+  if (st == FWI_OK) st = dalloc(c, &c->d_mu, (size_t)g.nmat);
+  if (st == FWI_OK) {
+    g.lam = c->d_lam;
+    g.mu = c->d_mu;
+    for (int b = 0; b < 4 && st == FWI_OK; b++)
+      if (cudaMemset(c->state[b], 0, sizeof(float) * sbytes) != cudaSuccess)
+        st = fail(c, FWI_E_CUDA, "state clear failed");
+  }
+  if (st != FWI_OK) {
+    fwi_destroy(c);
+    return st;
+  }
+  *out = c;
+  return FWI_OK;
+}
+
+void fwi_destroy(fwi_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (int b = 0; b < 4; b++) dfree(c->state[b]);
+  for (int ax = 0; ax < 3; ax++) {
+    dfree(c->d_alpha[ax]);
+    dfree(c->d_beta[ax]);
+  }
+  dfree(c->d_lam);
+  dfree(c->d_mu);
+  dfree(c->d_wave);
+  dfree(c->d_src_node);
+  dfree(c->d_src_vec);
+  dfree(c->d_rec_node);
+  dfree(c->d_rec_vec);
+  dfree(c->d_traces);
+  dfree(c->d_obs);
+  dfree(c->d_resid);
+  dfree(c->d_part);
+  dfree(c->d_J);
+  dfree(c->d_flag);
+  dfree(c->d_hist);
+  dfree(c->d_gl);
+  dfree(c->d_gm);
+  for (auto e : c->ev_free) cudaEventDestroy(e);
+  for (auto &p : c->ev_pending) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  delete c;
+}
+
+fwi_status fwi_get_dims(const fwi_ctx *c, int64_t dims[8]) {
+  if (!c || !dims) return FWI_E_INVAL;
+  dims[0] = c->geo.n[0];
+  dims[1] = c->geo.n[1];
+  dims[2] = c->geo.n[2];
+  dims[3] = c->geo.nnode;
+  dims[4] = c->geo.nmat;
+  dims[5] = c->geo.stride;
+  dims[6] = c->nelem;
+  dims[7] = c->npml_nodes;
+  return FWI_OK;
+}
+
+fwi_status fwi_set_material(fwi_ctx *c, const float *lambda, const float *mu, int on_device) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (!lambda || !mu) return fail(c, FWI_E_INVAL, "null material pointer");
+  const size_t n = (size_t)c->geo.nmat;
+  std::vector<float> hl(n), hm(n);
+  if (on_device) {
+    CUDA_TRY(c, cudaMemcpyAsync(hl.data(), lambda, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(hm.data(), mu, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(hl.data(), lambda, n * sizeof(float));
+    std::memcpy(hm.data(), mu, n * sizeof(float));
+  }
+  double vmax = 0.0;
+  for (size_t i = 0; i < n; i++) {
+    if (!std::isfinite(hl[i]) || !std::isfinite(hm[i]))
+      return fail(c, FWI_E_NONFINITE, "non-finite material value at node %zu", i);
+    if (!(hm[i] > 0.f) || !(hl[i] + 2.f * hm[i] > 0.f))
+      return fail(c, FWI_E_INVAL, "material at node %zu violates mu > 0, lambda + 2 mu > 0", i);
+    vmax = std::fmax(vmax, std::sqrt(((double)hl[i] + 2.0 * hm[i]) / c->cfg.rho));
+  }
+  const double cfl = c->cfg.dt * vmax / (0.5 * c->cfg.h);
+  if (cfl > 0.66)
+    return fail(c, FWI_E_UNSTABLE, "dt * vp_max / (h/2) = %.3f above the RK4 limit estimate 0.66", cfl);
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_lam, hl.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_mu, hm.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->have_material = true;
+  return FWI_OK;
+}
+
+fwi_status fwi_set_sources(fwi_ctx *c, int nshots, const int *node_ijk, const double *dir, int wavelet,
+                           const double *wparams) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (nshots < 1 || !node_ijk || !dir || !wparams) return fail(c, FWI_E_INVAL, "bad source arguments");
+  if (wavelet != FWI_WAVELET_RICKER && wavelet != FWI_WAVELET_GAUSS)
+    return fail(c, FWI_E_INVAL, "unknown wavelet %d", wavelet);
+  if (wavelet == FWI_WAVELET_GAUSS && !(wparams[1] > 0)) return fail(c, FWI_E_INVAL, "gauss sigma must be > 0");
+  std::vector<int64_t> nodes(nshots);
+  std::vector<float> vec(3 * (size_t)nshots);
+  for (int s = 0; s < nshots; s++) {
+    const int i = node_ijk[3 * s], j = node_ijk[3 * s + 1], k = node_ijk[3 * s + 2];
+    if (i < 0 || j < 0 || k < 0 || i >= c->geo.n[0] || j >= c->geo.n[1] || k >= c->geo.n[2])
+      return fail(c, FWI_E_INVAL, "source %d node (%d,%d,%d) outside the mesh", s, i, j, k);
+    if (is_dirichlet(c, i, j, k)) return fail(c, FWI_E_INVAL, "source %d on a fixed (Dirichlet) face", s);
+    nodes[s] = ((int64_t)k * c->geo.n[1] + j) * c->geo.n[0] + i;
+    const double minv = 1.0 / mass_u(c, i, j, k);
+    for (int d = 0; d < 3; d++) {
+      if (!std::isfinite(dir[3 * s + d])) return fail(c, FWI_E_NONFINITE, "non-finite source direction");
+      vec[3 * s + d] = (float)(dir[3 * s + d] * minv);
+    }
+  }
+  // wavelet samples at t = j dt / 2, j = 0 .. 2 nsteps (RK4 stage times), FP64 -> FP32
+  const int nw = 2 * c->cfg.nsteps + 1;
+  std::vector<float> wave(nw);
+  for (int j = 0; j < nw; j++) {
+    const double t = 0.5 * j * c->cfg.dt;
+    double r;
+    if (wavelet == FWI_WAVELET_RICKER) {
+      const double a = M_PI * wparams[0] * (t - wparams[1]);
+      r = wparams[2] * (1.0 - 2.0 * a * a) * std::exp(-a * a);
+    } else {
+      const double x = t - wparams[0];
+      r = wparams[2] * std::exp(-x * x / wparams[1]);
+    }
+    wave[j] = (float)r;
+  }
+  dfree(c->d_src_node);
+  dfree(c->d_src_vec);
+  dfree(c->d_wave);
+  TRY(dalloc(c, &c->d_src_node, (size_t)nshots));
+  TRY(dalloc(c, &c->d_src_vec, 3 * (size_t)nshots));
+  TRY(dalloc(c, &c->d_wave, (size_t)nw));
+  CUDA_TRY(c, cudaMemcpy(c->d_src_node, nodes.data(), sizeof(int64_t) * nshots, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_src_vec, vec.data(), sizeof(float) * 3 * nshots, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_wave, wave.data(), sizeof(float) * nw, cudaMemcpyHostToDevice));
+  c->nshots = nshots;
+  c->src_node = nodes;
+  c->src_dir.assign(dir, dir + 3 * (size_t)nshots);
+  c->wavelet = wavelet;
+  std::memcpy(c->wparams, wparams, sizeof c->wparams);
+  return FWI_OK;
+}
+
+fwi_status fwi_set_receivers(fwi_ctx *c, int nrec, const int *node_ijk) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (nrec < 1 || !node_ijk) return fail(c, FWI_E_INVAL, "bad receiver arguments");
+  std::vector<int64_t> nodes(nrec);
+  std::vector<float> vec(3 * (size_t)nrec);
+  for (int r = 0; r < nrec; r++) {
+    const int i = node_ijk[3 * r], j = node_ijk[3 * r + 1], k = node_ijk[3 * r + 2];
+    if (i < 0 || j < 0 || k < 0 || i >= c->geo.n[0] || j >= c->geo.n[1] || k >= c->geo.n[2])
+      return fail(c, FWI_E_INVAL, "receiver %d node (%d,%d,%d) outside the mesh", r, i, j, k);
+    if (is_dirichlet(c, i, j, k)) return fail(c, FWI_E_INVAL, "receiver %d on a fixed (Dirichlet) face", r);
+    nodes[r] = ((int64_t)k * c->geo.n[1] + j) * c->geo.n[0] + i;
+    const float minv = (float)(1.0 / mass_u(c, i, j, k));
+    vec[3 * r] = vec[3 * r + 1] = vec[3 * r + 2] = minv;
+  }
+  {
+    std::vector<int64_t> sorted = nodes;
+    std::sort(sorted.begin(), sorted.end());
+    for (int r = 1; r < nrec; r++)
+      if (sorted[r] == sorted[r - 1]) return fail(c, FWI_E_INVAL, "receivers must be distinct nodes");
+  }
+  dfree(c->d_rec_node);
+  dfree(c->d_rec_vec);
+  dfree(c->d_traces);
+  dfree(c->d_obs);
+  dfree(c->d_resid);
+  TRY(dalloc(c, &c->d_rec_node, (size_t)nrec));
+  TRY(dalloc(c, &c->d_rec_vec, 3 * (size_t)nrec));
+  CUDA_TRY(c, cudaMemcpy(c->d_rec_node, nodes.data(), sizeof(int64_t) * nrec, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_rec_vec, vec.data(), sizeof(float) * 3 * nrec, cudaMemcpyHostToDevice));
+  c->nrec = nrec;
+  c->rec_node = nodes;
+  return FWI_OK;
+}
+
+fwi_status fwi_forward(fwi_ctx *c, int shot0, int nshots, float *traces, int on_device) {
+  if (!c) return FWI_E_INVAL;
+  TRY(require_ready(c, shot0, nshots));
+  if (!traces) return fail(c, FWI_E_INVAL, "null traces");
+  TRY(ensure_trace_buffers(c));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  const size_t nt = (size_t)(c->cfg.nsteps + 1) * c->nrec * 3;
+  for (int s = 0; s < nshots; s++) {
+    TRY(forward_sweep(c, shot0 + s, nullptr));
+    CUDA_TRY(c, cudaMemcpyAsync(traces + s * nt, c->d_traces, nt * sizeof(float),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
+fwi_status fwi_misfit(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device, double *J) {
+  if (!c) return FWI_E_INVAL;
+  TRY(require_ready(c, shot0, nshots));
+  if (!observed || !J) return fail(c, FWI_E_INVAL, "null argument");
+  TRY(ensure_trace_buffers(c));
+  TRY(ensure_J(c, nshots));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  for (int s = 0; s < nshots; s++) {
+    TRY(forward_sweep(c, shot0 + s, nullptr));
+    fwi_status st;
+    const float *obs = observed_for_shot(c, observed, on_device, s, &st);
+    if (!obs) return st;
+    TRY(misfit_of_traces(c, obs, s));
+  }
+  return finish_J(c, nshots, J);
+}
+
+fwi_status fwi_adjoint_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device,
+                                double *J, double *g_lambda, double *g_mu) {
+  if (!c) return FWI_E_INVAL;
+  TRY(require_ready(c, shot0, nshots));
+  if (!observed || !g_lambda || !g_mu) return fail(c, FWI_E_INVAL, "null argument");
+  TRY(ensure_trace_buffers(c));
+  TRY(ensure_J(c, nshots));
+  const size_t nmat = (size_t)c->geo.nmat;
+  const size_t hbytes = (size_t)(c->cfg.nsteps + 1) * 3 * nmat;
+  TRY(dalloc(c, &c->d_hist, hbytes));
+  TRY(dalloc(c, &c->d_gl, nmat));
+  TRY(dalloc(c, &c->d_gm, nmat));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_gl, 0, sizeof(double) * nmat, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_gm, 0, sizeof(double) * nmat, c->stream));
+  const int N = c->cfg.nsteps;
+  const size_t hstep = 3 * nmat;
+  for (int s = 0; s < nshots; s++) {
+    TRY(forward_sweep(c, shot0 + s, c->d_hist));
+    fwi_status st;
+    const float *obs = observed_for_shot(c, observed, on_device, s, &st);
+    if (!obs) return st;
+    TRY(misfit_of_traces(c, obs, s));
+    // adjoint sweep in reversed time with the gradient time integral (C.1f)/(C.1g)
+    TRY(zero_state(c));
+    for (int m = 0; m < N; m++) {
+      TRY(rk4_step(c, true, m, 0, nullptr));
+      const int lvl = N - m - 1;  // adjoint state now holds w(t_lvl)
+      if (lvl > 0) {
+        const double wn = (lvl == N) ? 0.5 : 1.0;
+        cudaEvent_t e0;
+        time_begin(c, &e0);
+        fwi::launch_gradient(c->geo, c->state[0], c->d_hist + (size_t)lvl * hstep, wn * c->cfg.dt, c->d_gl,
+                             c->d_gm, c->stream);
+        time_end(c, e0, 1);
+        CUDA_TRY(c, cudaGetLastError());
+      }
+    }
+  }
+  fwi::launch_check_finite(c->d_gl, (int64_t)nmat, c->d_flag, c->stream);
+  fwi::launch_check_finite(c->d_gm, (int64_t)nmat, c->d_flag, c->stream);
+  c->t_launch[3] += 2;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  // stage the outputs only after the finite check: copy into the caller's arrays last
+  double Jv = 0.0;
+  TRY(finish_J(c, nshots, &Jv));
+  CUDA_TRY(c, cudaMemcpyAsync(g_lambda, c->d_gl, sizeof(double) * nmat, kind, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(g_mu, c->d_gm, sizeof(double) * nmat, kind, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (J) *J = Jv;
+  return FWI_OK;
+}
+
+fwi_status fwi_get_mass_tilde(fwi_ctx *c, double *mtilde) {
+  if (!c || !mtilde) return FWI_E_INVAL;
+  // (C.1a) with LGL quadrature: sum over the interior elements around node i of W_i detJ
+  const fwi::Geo &g = c->geo;
+  const double hh = 0.5 * c->cfg.h, wd = hh * hh * hh;
+  for (int k = 0; k < g.m[2]; k++)
+    for (int j = 0; j < g.m[1]; j++)
+      for (int i = 0; i < g.m[0]; i++) {
+        const int cc[3] = {i, j, k};
+        double w = wd, nel = 1.0;
+        for (int ax = 0; ax < 3; ax++) {
+          w *= (cc[ax] & 1) ? 4.0 / 3.0 : 1.0 / 3.0;
+          nel *= (cc[ax] & 1) ? 1 : ((cc[ax] >= 2) + (cc[ax] <= g.m[ax] - 3));
+        }
+        mtilde[((int64_t)k * g.m[1] + j) * g.m[0] + i] = w * nel;
+      }
+  return FWI_OK;
+}
+
+fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int on_device) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (!c->have_material) return fail(c, FWI_E_STATE, "material not set");
+  if (!state || !rate) return fail(c, FWI_E_INVAL, "null argument");
+  const size_t n = (size_t)fwi::kFields * c->geo.stride;
+  const float *in = state;
+  float *out = rate;
+  if (!on_device) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->state[1], state, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    in = c->state[1];
+    out = c->state[2];
+  }
+  fwi::StageArgs a{};
+  a.Y = in;
+  a.X = in;
+  a.out = out;
+  a.stage = 0;
+  TRY(stage(c, adjoint != 0, a));
+  if (!on_device)
+    CUDA_TRY(c, cudaMemcpyAsync(rate, c->state[2], n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (!on_device) {
+    CUDA_TRY(c, cudaMemsetAsync(c->state[1], 0, n * sizeof(float), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->state[2], 0, n * sizeof(float), c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  return FWI_OK;
+}
+
+fwi_status fwi_set_timing(fwi_ctx *c, int enable) {
+  if (!c) return FWI_E_INVAL;
+  c->timing = enable != 0;
+  return FWI_OK;
+}
+
+fwi_status fwi_get_timing(fwi_ctx *c, int which, double *ms, int64_t *launches) {
+  if (!c || which < 0 || which > 3) return FWI_E_INVAL;
+  TRY(time_flush(c));
+  if (ms) *ms = c->t_ms[which];
+  if (launches) *launches = c->t_launch[which];
+  return FWI_OK;
+}
+
+fwi_status fwi_reset_timing(fwi_ctx *c) {
+  if (!c) return FWI_E_INVAL;
+  TRY(time_flush(c));
+  for (int i = 0; i < 4; i++) {
+    c->t_ms[i] = 0;
+    c->t_launch[i] = 0;
+  }
+  return FWI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// fwi_internal.h -- shared declarations between the C-ABI host code (fwi_api.cu)
+// and the CUDA kernels (fwi_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fwi {
+
+constexpr int kFields = 27;  // 3 levels x (3 displacement + 6 stress components)
+constexpr int kLevelFields = 9;
+
+// Mesh geometry and per-node coefficient sources, passed by value to kernels.
+struct Geo {
+  int n[3];         // nodes per axis (NI, NJ, NK)
+  int lo[3], hi[3]; // interior element range per axis, [lo, hi)
+  int m[3];         // material-grid nodes per axis (2nx+1, 2ny+1, 2nz+1)
+  int top_dir;      // 1: displacement fixed on k = 0 (top PML)
+  int64_t stride;   // floats per state field (>= node count, padded)
+  int64_t nnode, nmat;
+  float inv_h;      // 1 / h
+  float rho;
+  float wdetj;      // (h/2)^3
+  const float *alpha[3];  // stretch alpha_s at each node coordinate, per axis
+  const float *beta[3];   // stretch beta_s, 1/s
+  const float *lam, *mu;  // interior material grid [k][j][i]
+};
+
+// One RK4 stage over every node (see fwi_kernels.cu).
+//  stage 0: out = rate(Y)                   (fwi_rhs)
+//  stage 1..3: out = X + cdt * rate(Y)
+//  stage 4: out = (-X + Y2 + 2 Y3 + Y)/3 + cdt * rate(Y)   (out may alias X)
+struct StageArgs {
+  const float *Y;    // stage input
+  const float *X;    // step start
+  const float *Y2, *Y3;
+  float *out;
+  float cdt;
+  int stage;
+  float *hist;       // stage 4: interior displacement written here as [3][nmat], or null
+};
+
+void launch_stage(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+
+// Point loads on level-2 displacement rows of buffer `buf`:
+// buf[9*2 + c][node[p]] += cdt * amp_p * vec[p][c], where
+//   mode 0 (sources): amp_p = wave[widx0] (or 0.5*(wave[widx0]+wave[widx1]))
+//   mode 1 (receiver residuals): amp_p = 1 and vec = minv * (resid[t0][p] (+ resid[t1][p])/2)
+struct PointArgs {
+  float *buf;
+  int64_t stride;
+  int npts;
+  const int64_t *node;
+  const float *vec;      // [npts][3]: dir * Minv (sources) or Minv replicated (receivers)
+  const float *table;    // sources: wavelet samples at t = j dt/2; receivers: residual [nt][npts][3]
+  int i0, i1;            // sample indices (i1 < 0: single sample)
+  float cdt;
+  int mode;
+};
+void launch_point(const PointArgs &p, cudaStream_t s);
+
+// traces[r][c] = buf[9 + c][node[r]]
+void launch_sample(const float *buf, int64_t stride, int nrec, const int64_t *node, float *traces,
+                   cudaStream_t s);
+
+// Gradient integrand of (C.1f)/(C.1g) at one time level, accumulated in FP64:
+// gl[i] -= wdt * sum_e W detJ (div w)(div u), gm[i] -= wdt * sum_e W detJ 2 eps(w):eps(u).
+void launch_gradient(const Geo &g, const float *w_state, const float *u_hist, double wdt, double *gl,
+                     double *gm, cudaStream_t s);
+
+// resid = traces - observed (n values); partial sums of w_n dt e^2 / 2 per block into part;
+// flag set to 1 on a non-finite trace value.
+int misfit_blocks(int64_t n);
+void launch_residual(const float *traces, const float *observed, float *resid, int64_t n,
+                     int64_t per_step, int nsteps, double dt, double *part, int *flag, cudaStream_t s);
+void launch_sum(const double *part, int nblocks, double *out, cudaStream_t s);
+
+// flag = 1 if any value of x (n doubles) is not finite.
+void launch_check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);
+
+}  // namespace fwi
