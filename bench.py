@@ -161,7 +161,6 @@ def run_reference(args, w):
     for _ in range(args.steps):
         vals.append(cpu_baseline(w, steps_sample=1)["value"])
     total = time.perf_counter() - t0
-    cb = cpu_baseline.__defaults__  # noqa: F841
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
@@ -176,6 +175,21 @@ def run_reference(args, w):
     return 0
 
 
+def profile_forward(w, nsteps, repeats):
+    """Short forward sweeps on the benchmark mesh (1 GB of state, no history) for ncu captures."""
+    import torch
+
+    w.nsteps = nsteps
+    dev = torch.device("cuda", 0)
+    ctx, obs, _ = setup(w, torch, dev)
+    for _ in range(repeats):
+        ctx.forward(out=obs)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_forward": w.name, "nsteps": nsteps, "repeats": repeats}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,8 +198,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-forward", type=int, default=0, metavar="NSTEPS",
+                    help="profiling aid: run only short forward sweeps (NSTEPS RK4 steps) on the same mesh")
     args = ap.parse_args()
     w = workload()
+    if args.profile_forward:
+        return profile_forward(w, args.profile_forward, max(args.steps, 1))
     if args.impl == "reference":
         return run_reference(args, w)
 

@@ -220,7 +220,6 @@ def test_error_paths():
         Context(0, 1, 1, 1, 1.0, 1e-4, 10)
     assert e.value.name == "FWI_E_INVAL"
     with _ctx(w) as ctx:
-        obs = np.zeros(ctx.trace_shape(1), dtype=np.float32)
         with pytest.raises(FWIError) as e:
             ctx.forward()
         assert e.value.name == "FWI_E_STATE"
@@ -246,4 +245,6 @@ def test_error_paths():
             ctx.forward(shot0=1)
         assert e.value.name == "FWI_E_INVAL"
         # the context stays usable after these errors
-        assert np.isfinite(ctx.misfit(obs))
+        obs = np.zeros(ctx.trace_shape(1), dtype=np.float32)
+        J = ctx.misfit(obs)
+        assert np.isfinite(J) and J > 0
