@@ -173,6 +173,21 @@ fwi_status fwi_set_timing(fwi_ctx *ctx, int enable);
 fwi_status fwi_get_timing(fwi_ctx *ctx, int which, double *ms, int64_t *launches);
 fwi_status fwi_reset_timing(fwi_ctx *ctx);
 
+/* Misfit of traces that are already on the GPU, for callers that cannot allocate
+ * device memory (code running where cudaMalloc is not allowed or where the host
+ * application owns the whole device-memory budget). No counterpart in the paper:
+ * it computes the same J as fwi_misfit's reduction, from caller-supplied traces.
+ * traces, observed: device arrays of (nsteps+1)*nrec*3 floats ([n][r][c]);
+ * J: host. The call allocates nothing: its scratch is a fixed 512 KiB device
+ * array inside the library, which every GPU that loads the library keeps until
+ * the process exits. The first call on a device looks up that array's address
+ * (do it before any stream capture). Calls share the array, so calls that
+ * overlap on the GPU race. Errors: FWI_E_INVAL (null pointers, nrec < 1,
+ * dt <= 0, or nsteps + 1 > 65536, the scratch limit), FWI_E_NONFINITE (a trace
+ * value is NaN/Inf), FWI_E_CUDA. */
+fwi_status fwi_trace_misfit_noalloc(const float *traces, const float *observed, int nsteps, int nrec,
+                                    double dt, void *cuda_stream, double *J);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,7 +37,7 @@ class _Config(C.Structure):
 EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_get_dims",
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
-           "fwi_get_timing", "fwi_reset_timing")
+           "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc")
 
 _lib = None
 
@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_set_timing.argtypes = [P, I]
     lib.fwi_get_timing.argtypes = [P, I, D, I64]
     lib.fwi_reset_timing.argtypes = [P]
+    lib.fwi_trace_misfit_noalloc.argtypes = [P, P, I, I, C.c_double, P, D]
     for name in EXPORTS:
         if name not in ("fwi_destroy", "fwi_last_error", "fwi_status_string"):
             getattr(lib, name).restype = I
