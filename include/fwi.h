@@ -98,8 +98,8 @@ const char *fwi_status_string(fwi_status s);
 /* Sizes: dims[0..2] nodes per axis (NI, NJ, NK), dims[3] node count,
  * dims[4] interior (material) node count, dims[5] field stride in floats of the
  * state layout used by fwi_rhs, dims[6] number of elements, dims[7] number of
- * PML nodes. */
-fwi_status fwi_get_dims(const fwi_ctx *ctx, int64_t dims[8]);
+ * PML nodes, dims[8] row pitch PX of that layout (NI rounded up to 4). */
+fwi_status fwi_get_dims(const fwi_ctx *ctx, int64_t dims[9]);
 
 /* Set the trial Lame parameters (D4: nodal values on the interior nodes,
  * [k][j][i], Pa; host or device). Checks finiteness, mu > 0, lambda + 2 mu > 0
@@ -159,7 +159,9 @@ fwi_status fwi_get_mass_tilde(fwi_ctx *ctx, double *mtilde);
  *   z = D y1(T - s), z' = -D y2(T - s), zbar = -D y0(T - s) this is (15).
  * state and rate: 27 fields of dims[5] floats each (host or device); field
  * 9*l + c holds level l (0: history, 1: value, 2: rate) and component c
- * (0..2 displacement x,y,z; 3..8 stress xx,yy,zz,yz,xz,xy) of every node.
+ * (0..2 displacement x,y,z; 3..8 stress xx,yy,zz,yz,xz,xy) of every node;
+ * node (i, j, k) sits at offset (k * NJ + j) * PX + i of a field (PX = dims[8];
+ * the padding entries i >= NI must be zero).
  * Displacement fields must be zero on the Dirichlet faces and history / stress
  * fields zero off the PML nodes. Errors: FWI_E_STATE (no material). */
 fwi_status fwi_rhs(fwi_ctx *ctx, int adjoint, const float *state, float *rate, int on_device);

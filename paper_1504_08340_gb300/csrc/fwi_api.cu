@@ -23,6 +23,8 @@ struct fwi_ctx {
   fwi_config cfg{};
   fwi::Geo geo{};
   cudaStream_t stream = nullptr;
+  cudaStream_t side[2] = {nullptr, nullptr};  // the stage's kernels fork onto these and join back
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   bool cuda_failed = false;
   std::string err;
   int64_t nelem = 0, npml_nodes = 0;
@@ -32,6 +34,7 @@ struct fwi_ctx {
   float *d_beta[3] = {nullptr, nullptr, nullptr};
   std::vector<double> h_alpha[3], h_beta[3];
   float *d_lam = nullptr, *d_mu = nullptr;
+  int *d_shell = nullptr, *d_face = nullptr;
   bool have_material = false;
 
   int nshots = 0;
@@ -189,7 +192,26 @@ fwi_status time_flush(fwi_ctx *c) {
 fwi_status stage(fwi_ctx *c, bool adj, const fwi::StageArgs &a) {
   cudaEvent_t e0;
   time_begin(c, &e0);
-  fwi::launch_stage(c->geo, a, adj, c->stream);
+#ifdef FWI_SERIAL_STAGE
+  fwi::launch_interior(c->geo, a, c->stream);
+  fwi::launch_shell(c->geo, a, adj, c->stream);
+  fwi::launch_pml(c->geo, a, adj, c->stream);
+  if (false) {
+#else
+  {
+#endif
+  // fork: interior and interface/face kernels on the side streams, bulk PML here
+  CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->stream));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->side[0], c->ev_fork, 0));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->side[1], c->ev_fork, 0));
+  fwi::launch_interior(c->geo, a, c->side[0]);
+  fwi::launch_shell(c->geo, a, adj, c->side[1]);
+  fwi::launch_pml(c->geo, a, adj, c->stream);
+  CUDA_TRY(c, cudaEventRecord(c->ev_join[0], c->side[0]));
+  CUDA_TRY(c, cudaEventRecord(c->ev_join[1], c->side[1]));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_join[0], 0));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_join[1], 0));
+  }
   time_end(c, e0, 0);
   CUDA_TRY(c, cudaGetLastError());
   if (c->ev_pending.size() > 400000) TRY(time_flush(c));
@@ -373,7 +395,9 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   if (cfg->npml == 0 && cfg->top_pml) return FWI_E_INVAL;
   const int64_t nI = 2LL * (cfg->nx + 2LL * cfg->npml) + 1, nJ = 2LL * (cfg->ny + 2LL * cfg->npml) + 1,
                 nK = 2LL * (cfg->nz + cfg->npml + (cfg->top_pml ? cfg->npml : 0)) + 1;
-  if (nI * nJ * nK > (1LL << 34)) return FWI_E_INVAL;
+  // the PML stage kernel addresses the 27 state fields with 32-bit offsets
+  const int64_t px = (nI + 3) / 4 * 4;
+  if (27 * (px * nJ * nK + 64) >= (1LL << 31)) return FWI_E_INVAL;
   fwi_ctx *c = new (std::nothrow) fwi_ctx();
   if (!c) return FWI_E_NOMEM;
   c->cfg = *cfg;
@@ -381,6 +405,7 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   fwi::Geo &g = c->geo;
   g.n[0] = (int)nI;
   g.n[1] = (int)nJ;
+  g.px = (int)px;
   g.n[2] = (int)nK;
   g.lo[0] = cfg->npml;
   g.lo[1] = cfg->npml;
@@ -392,9 +417,18 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   g.m[1] = 2 * cfg->ny + 1;
   g.m[2] = 2 * cfg->nz + 1;
   g.top_dir = cfg->top_pml ? 1 : 0;
+  for (int ax = 0; ax < 3; ax++) {
+    // coordinates all of whose elements along this axis are interior, minus fixed faces
+    const int Nax = (g.n[ax] - 1) / 2;
+    int lo_c = 2 * g.lo[ax] + (g.lo[ax] > 0 ? 1 : 0);
+    int hi_c = 2 * g.hi[ax] - (g.hi[ax] < Nax ? 1 : 0);
+    const int first_free = (ax == 2 && !g.top_dir) ? 0 : 1;
+    g.box_lo[ax] = lo_c > first_free ? lo_c : first_free;
+    g.box_hi[ax] = hi_c < g.n[ax] - 2 ? hi_c : g.n[ax] - 2;
+  }
   g.nnode = nI * nJ * nK;
   g.nmat = (int64_t)g.m[0] * g.m[1] * g.m[2];
-  g.stride = (g.nnode + 63) / 64 * 64;
+  g.stride = (px * nJ * nK + 63) / 64 * 64;
   g.inv_h = (float)(1.0 / cfg->h);
   g.rho = (float)cfg->rho;
   g.wdetj = (float)(0.125 * cfg->h * cfg->h * cfg->h);
@@ -435,6 +469,12 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
     }
   }
   fwi_status st = FWI_OK;
+  for (int i = 0; i < 2 && st == FWI_OK; i++)
+    if (cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+      st = fail(c, FWI_E_CUDA, "stream setup failed");
+  if (st == FWI_OK && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    st = fail(c, FWI_E_CUDA, "event setup failed");
   const size_t sbytes = (size_t)fwi::kFields * g.stride;
   for (int b = 0; b < 4 && st == FWI_OK; b++) st = dalloc(c, &c->state[b], sbytes);
   for (int ax = 0; ax < 3 && st == FWI_OK; ax++) {
@@ -451,6 +491,59 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
       st = fail(c, FWI_E_CUDA, "stretch table upload failed");
     g.alpha[ax] = c->d_alpha[ax];
     g.beta[ax] = c->d_beta[ax];
+  }
+  if (st == FWI_OK && fwi::prepare_interior() != cudaSuccess) st = fail(c, FWI_E_CUDA, "kernel attribute setup failed");
+  if (st == FWI_OK) {
+    // interface shell: closed interior box minus the open box of the interior kernel
+    std::vector<int> shell;
+    const int c0[3] = {2 * g.lo[0], 2 * g.lo[1], g.top_dir ? 2 * g.lo[2] : 0};
+    const int c1[3] = {2 * g.hi[0], 2 * g.hi[1], 2 * g.hi[2]};
+    for (int k = c0[2]; k <= c1[2]; k++)
+      for (int j = c0[1]; j <= c1[1]; j++)
+        for (int i = c0[0]; i <= c1[0]; i++) {
+          const bool in_open = i >= g.box_lo[0] && i <= g.box_hi[0] && j >= g.box_lo[1] && j <= g.box_hi[1] &&
+                               k >= g.box_lo[2] && k <= g.box_hi[2];
+          if (!in_open) shell.push_back((k * g.n[1] + j) * g.px + i);
+        }
+    // PML nodes on the outer faces of the grid: outside the closed box, on a face
+    std::vector<int> face;
+    for (int k = 0; k < g.n[2]; k++)
+      for (int j = 0; j < g.n[1]; j++)
+        for (int i = 0; i < g.n[0]; i++) {
+          const bool on_face = i == 0 || i == g.n[0] - 1 || j == 0 || j == g.n[1] - 1 || k == 0 || k == g.n[2] - 1;
+          if (!on_face) continue;
+          const bool in_closed = i >= c0[0] && i <= c1[0] && j >= c0[1] && j <= c1[1] && k >= c0[2] && k <= c1[2];
+          if (!in_closed) face.push_back((k * g.n[1] + j) * g.px + i);
+        }
+    // group the list entries by coordinate parity (and by face position inside a group)
+    // so that the 32 nodes of a warp take the same side-type branches
+    auto by_parity = [&](std::vector<int> &v) {
+      std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+        auto key = [&](int n) {
+          const int i = n % g.px, r = n / g.px, j = r % g.n[1], k = r / g.n[1];
+          return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        };
+        return key(a) < key(b);
+      });
+    };
+    by_parity(shell);
+    by_parity(face);
+    g.nface = (int)face.size();
+    if (g.nface > 0) {
+      st = dalloc(c, &c->d_face, face.size());
+      if (st == FWI_OK &&
+          cudaMemcpy(c->d_face, face.data(), sizeof(int) * face.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(c, FWI_E_CUDA, "face list upload failed");
+      g.face = c->d_face;
+    }
+    g.nshell = (int)shell.size();
+    if (g.nshell > 0) {
+      st = dalloc(c, &c->d_shell, shell.size());
+      if (st == FWI_OK &&
+          cudaMemcpy(c->d_shell, shell.data(), sizeof(int) * shell.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(c, FWI_E_CUDA, "shell list upload failed");
+      g.shell = c->d_shell;
+    }
   }
   if (st == FWI_OK) st = dalloc(c, &c->d_lam, (size_t)g.nmat);
   if (st == FWI_OK) st = dalloc(c, &c->d_mu, (size_t)g.nmat);
@@ -479,6 +572,8 @@ void fwi_destroy(fwi_ctx *c) {
   }
   dfree(c->d_lam);
   dfree(c->d_mu);
+  dfree(c->d_shell);
+  dfree(c->d_face);
   dfree(c->d_wave);
   dfree(c->d_src_node);
   dfree(c->d_src_vec);
@@ -493,6 +588,14 @@ void fwi_destroy(fwi_ctx *c) {
   dfree(c->d_hist);
   dfree(c->d_gl);
   dfree(c->d_gm);
+  for (int i = 0; i < 2; i++) {
+    if (c->side[i]) {
+      cudaStreamSynchronize(c->side[i]);
+      cudaStreamDestroy(c->side[i]);
+    }
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   for (auto e : c->ev_free) cudaEventDestroy(e);
   for (auto &p : c->ev_pending) {
     cudaEventDestroy(p.first);
@@ -501,7 +604,7 @@ void fwi_destroy(fwi_ctx *c) {
   delete c;
 }
 
-fwi_status fwi_get_dims(const fwi_ctx *c, int64_t dims[8]) {
+fwi_status fwi_get_dims(const fwi_ctx *c, int64_t dims[9]) {
   if (!c || !dims) return FWI_E_INVAL;
   dims[0] = c->geo.n[0];
   dims[1] = c->geo.n[1];
@@ -511,6 +614,7 @@ fwi_status fwi_get_dims(const fwi_ctx *c, int64_t dims[8]) {
   dims[5] = c->geo.stride;
   dims[6] = c->nelem;
   dims[7] = c->npml_nodes;
+  dims[8] = c->geo.px;
   return FWI_OK;
 }
 
@@ -561,7 +665,7 @@ fwi_status fwi_set_sources(fwi_ctx *c, int nshots, const int *node_ijk, const do
     if (i < 0 || j < 0 || k < 0 || i >= c->geo.n[0] || j >= c->geo.n[1] || k >= c->geo.n[2])
       return fail(c, FWI_E_INVAL, "source %d node (%d,%d,%d) outside the mesh", s, i, j, k);
     if (is_dirichlet(c, i, j, k)) return fail(c, FWI_E_INVAL, "source %d on a fixed (Dirichlet) face", s);
-    nodes[s] = ((int64_t)k * c->geo.n[1] + j) * c->geo.n[0] + i;
+    nodes[s] = ((int64_t)k * c->geo.n[1] + j) * c->geo.px + i;
     const double minv = 1.0 / mass_u(c, i, j, k);
     for (int d = 0; d < 3; d++) {
       if (!std::isfinite(dir[3 * s + d])) return fail(c, FWI_E_NONFINITE, "non-finite source direction");
@@ -611,7 +715,7 @@ fwi_status fwi_set_receivers(fwi_ctx *c, int nrec, const int *node_ijk) {
     if (i < 0 || j < 0 || k < 0 || i >= c->geo.n[0] || j >= c->geo.n[1] || k >= c->geo.n[2])
       return fail(c, FWI_E_INVAL, "receiver %d node (%d,%d,%d) outside the mesh", r, i, j, k);
     if (is_dirichlet(c, i, j, k)) return fail(c, FWI_E_INVAL, "receiver %d on a fixed (Dirichlet) face", r);
-    nodes[r] = ((int64_t)k * c->geo.n[1] + j) * c->geo.n[0] + i;
+    nodes[r] = ((int64_t)k * c->geo.n[1] + j) * c->geo.px + i;
     const float minv = (float)(1.0 / mass_u(c, i, j, k));
     vec[3 * r] = vec[3 * r + 1] = vec[3 * r + 2] = minv;
   }

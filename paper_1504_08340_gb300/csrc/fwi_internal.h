@@ -13,9 +13,11 @@ constexpr int kLevelFields = 9;
 // Mesh geometry and per-node coefficient sources, passed by value to kernels.
 struct Geo {
   int n[3];         // nodes per axis (NI, NJ, NK)
+  int px;           // row pitch: node (i, j, k) is at (k * NJ + j) * px + i; px = NI rounded up to 4
   int lo[3], hi[3]; // interior element range per axis, [lo, hi)
   int m[3];         // material-grid nodes per axis (2nx+1, 2ny+1, 2nz+1)
   int top_dir;      // 1: displacement fixed on k = 0 (top PML)
+  int box_lo[3], box_hi[3];  // inclusive node box whose elements are all interior (no fixed faces)
   int64_t stride;   // floats per state field (>= node count, padded)
   int64_t nnode, nmat;
   float inv_h;      // 1 / h
@@ -24,6 +26,10 @@ struct Geo {
   const float *alpha[3];  // stretch alpha_s at each node coordinate, per axis
   const float *beta[3];   // stretch beta_s, 1/s
   const float *lam, *mu;  // interior material grid [k][j][i]
+  const int *shell;       // node numbers of the interface shell (see shell_kernel)
+  int nshell;
+  const int *face;        // node numbers of the PML nodes on the grid's outer faces
+  int nface;
 };
 
 // One RK4 stage over every node (see fwi_kernels.cu).
@@ -40,7 +46,18 @@ struct StageArgs {
   float *hist;       // stage 4: interior displacement written here as [3][nmat], or null
 };
 
-void launch_stage(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+// One RK4 stage is four kernels writing disjoint node sets; they read the same
+// input and may run concurrently on different streams:
+//  launch_interior: nodes all of whose elements are interior (fwi_interior.cu);
+//  launch_pml:      nodes all of whose elements are PML, off the outer faces (fwi_pml.cu);
+//  launch_shell:    the interface shell (fwi_stage.cu) and the PML nodes on the
+//                   outer faces of the grid (launch_pml_face, fwi_pml.cu).
+void launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s);
+void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+void launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+void launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+// raises the interior kernel's shared-memory limit on the current device
+cudaError_t prepare_interior();
 
 // Point loads on level-2 displacement rows of buffer `buf`:
 // buf[9*2 + c][node[p]] += cdt * amp_p * vec[p][c], where

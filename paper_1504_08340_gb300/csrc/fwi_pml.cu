@@ -1,0 +1,563 @@
+// fwi_pml.cu -- RK4 stage kernel for the nodes all of whose elements are PML
+// elements ("deep" PML nodes: the bulk of the PML buffer of Fig. 3).
+//
+// At such a node every element-level sum of (3a)/(3b) (Sec. 2 of
+// arXiv:1504.08340) runs over all ns_x ns_y ns_z elements around the node, and
+// with the lumped masses it collapses to symmetric one-dimensional stencils:
+//  - S rows: the element-summed derivative divided by the element count is the
+//    average over the sides along j of the one-sided derivatives,
+//      D_j v = (v[c+1] - v[c-1]) / h                           (c odd)
+//      D_j v = (v[c-2] - 4 v[c-1] + 4 v[c+1] - v[c+2]) / (2h)    (c even, two sides)
+//      one-sided (-3 v0 + 4 v1 - v2)/h or (v-2 - 4 v-1 + 3 v0)/h on the outer faces;
+//    H_ij = Le_jj D_j udot_i + Lp_jj D_j u_i + Lw_jj D_j ubar_i and
+//    S'' = (tau(P(H)) - b S' - c S - d Sbar) / a   (adjoint: P(H) in place of tau(P(H)))
+//  - u rows: (1/w_j) times the line quadrature of d phi_a/dx_j divided by the
+//    element count is exactly -D_j, except on the free top face where the one-sided
+//    quadrature (-3 g0 - 4 g1 + g2)/h keeps its centre term (the traction-free
+//    boundary of (2b)); so
+//      u'' = (sum_j D_j Q_ij) / (rho a) - (b u' + c u + d ubar) / a,
+//      Q_ij = Le_jj Sdot_ij + Lp_jj S_ij + Lw_jj Sbar_ij  (adjoint: tau(T) in place of S).
+// Lambda_jj does not depend on x_j, so it is the node's value along the j-line.
+//
+// Threads own node pairs (even x, odd x) of row segments of the PML region
+// (outside the closed interior box), with 32-bit field offsets.
+#include <cuda_runtime.h>
+
+#include "fwi_internal.h"
+
+namespace fwi {
+namespace {
+
+enum { kSC = 0, kSLR = 1, kSR = 2, kSL = 3 };  // odd, even (both sides), first node, last node
+
+__device__ __forceinline__ int side_kind(int c, int n) {
+  return (c & 1) ? kSC : (c == 0 ? kSR : (c == n - 1 ? kSL : kSLR));
+}
+
+// averaged element-wise derivative (times h) of f at offset o, axis stride s
+__device__ __forceinline__ float dav(const float *__restrict__ f, int o, int s, int kind) {
+  switch (kind) {
+    case kSC: return __ldg(f + o + s) - __ldg(f + o - s);
+    case kSLR: return 0.5f * (__ldg(f + o - 2 * s) - 4.f * __ldg(f + o - s) + 4.f * __ldg(f + o + s) - __ldg(f + o + 2 * s));
+    case kSR: return -3.f * __ldg(f + o) + 4.f * __ldg(f + o + s) - __ldg(f + o + 2 * s);
+    default: return __ldg(f + o - 2 * s) - 4.f * __ldg(f + o - s) + 3.f * __ldg(f + o);
+  }
+}
+
+// divergence part of the u rows (times h): +D_j for interior kinds; the free top face
+// (first node along z, one element) keeps the full one-sided quadrature.
+__device__ __forceinline__ float ddiv(float g_m2, float g_m1, float g0, float g_p1, float g_p2, int kind) {
+  if (kind == kSC) return g_p1 - g_m1;
+  if (kind == kSLR) return 0.5f * (g_m2 - 4.f * g_m1 + 4.f * g_p1 - g_p2);
+  return 3.f * g0 + 4.f * g_p1 - g_p2;  // kSR on the free surface: -(-3 g0 - 4 g1 + g2)
+}
+
+__host__ __device__ constexpr int sym(int i, int j) { return i == j ? i : (i + j == 1 ? 5 : (i + j == 2 ? 4 : 3)); }
+
+struct Region {
+  int nbox;
+  int lo[6][3], hi[6][3];  // inclusive node boxes
+  int rows_before[7];      // prefix sums of rows (J, K pairs) per box
+};
+
+__device__ __forceinline__ float stage_value(const StageArgs &a, int idx, float yv, float rate) {
+  if (a.stage == 0) return rate;
+  if (a.stage < 4) return __ldcs(a.X + idx) + a.cdt * rate;
+  return (-__ldcs(a.X + idx) + __ldcs(a.Y2 + idx) + 2.f * __ldcs(a.Y3 + idx) + yv) * (1.f / 3.f) + a.cdt * rate;
+}
+
+template <bool ADJ>
+__device__ void pml_node(const Geo &g, const StageArgs &a, int I, int J, int K) {
+  const int S = (int)g.stride;
+  const int node = (K * g.n[1] + J) * g.px + I;
+  const int st[3] = {1, g.px, g.px * g.n[1]};
+  const int kind[3] = {side_kind(I, g.n[0]), side_kind(J, g.n[1]), side_kind(K, g.n[2])};
+  const bool dir = I == 0 || I == g.n[0] - 1 || J == 0 || J == g.n[1] - 1 || K == g.n[2] - 1 ||
+                   (g.top_dir && K == 0);
+  const float *__restrict__ Y = a.Y;
+  const float alx = __ldg(g.alpha[0] + I), aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
+  const float bex = __ldg(g.beta[0] + I), bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
+  const float ca = alx * aly * alz;
+  const float cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
+  const float cc = alx * bey * bez + bex * aly * bez + bex * bey * alz;
+  const float cd = bex * bey * bez;
+  const float Le[3] = {aly * alz, alx * alz, alx * aly};
+  const float Lp[3] = {aly * bez + bey * alz, alx * bez + bex * alz, alx * bey + bex * aly};
+  const float Lw[3] = {bey * bez, bex * bez, bex * bey};
+  const float inv_a = 1.f / ca;
+  const float inv_h = g.inv_h;
+  float lam = 0.f, mu = 0.f;
+  {
+    int i = I - 2 * g.lo[0], j = J - 2 * g.lo[1], k = K - 2 * g.lo[2];
+    i = i < 0 ? 0 : (i >= g.m[0] ? g.m[0] - 1 : i);
+    j = j < 0 ? 0 : (j >= g.m[1] ? g.m[1] - 1 : j);
+    k = k < 0 ? 0 : (k >= g.m[2] ? g.m[2] - 1 : k);
+    const int mi = (k * g.m[1] + j) * g.m[0] + i;
+    if (!ADJ) {
+      lam = __ldg(g.lam + mi);
+      mu = __ldg(g.mu + mi);
+    }
+  }
+
+  // ---- displacement rows
+  if (!dir) {
+    float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      const int k = (j + 1) % 3, l = (j + 2) % 3;
+      const int kd = kind[j];
+      const int s = st[j];
+      const float Lv[3] = {Lw[j], Lp[j], Le[j]};
+      // Q column j at offsets -2..2 along j (only the ones the kind uses)
+      float q[3][5];
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int d = 0; d < 5; d++) q[c][d] = 0.f;
+#pragma unroll
+      for (int d = 0; d < 5; d++) {
+        const int off = d - 2;
+        const bool used = kd == kSC ? (off == -1 || off == 1)
+                                    : (kd == kSLR ? off != 0 : off >= 0);
+        if (!used) continue;
+        const int o = node + off * s;
+        float vj = 0.f, vk = 0.f, vl = 0.f;
+        if (!ADJ) {
+#pragma unroll
+          for (int lv = 0; lv < 3; lv++) {
+            const float *b = Y + (9 * lv + 3) * S;
+            vj += Lv[lv] * __ldg(b + sym(j, j) * S + o);
+            vk += Lv[lv] * __ldg(b + sym(k, j) * S + o);
+            vl += Lv[lv] * __ldg(b + sym(l, j) * S + o);
+          }
+        } else {
+          int cq[3] = {I, J, K};
+          cq[j] += off;
+          int i2 = cq[0] - 2 * g.lo[0], j2 = cq[1] - 2 * g.lo[1], k2 = cq[2] - 2 * g.lo[2];
+          i2 = i2 < 0 ? 0 : (i2 >= g.m[0] ? g.m[0] - 1 : i2);
+          j2 = j2 < 0 ? 0 : (j2 >= g.m[1] ? g.m[1] - 1 : j2);
+          k2 = k2 < 0 ? 0 : (k2 >= g.m[2] ? g.m[2] - 1 : k2);
+          const int mq = (k2 * g.m[1] + j2) * g.m[0] + i2;
+          const float lq = __ldg(g.lam + mq), muq = __ldg(g.mu + mq);
+#pragma unroll
+          for (int lv = 0; lv < 3; lv++) {
+            const float *b = Y + (9 * lv + 3) * S;
+            const float tjj = __ldg(b + j * S + o), tkk = __ldg(b + k * S + o), tll = __ldg(b + l * S + o);
+            vj += Lv[lv] * (2.f * muq * tjj + lq * (tjj + tkk + tll));
+            vk += Lv[lv] * (muq * __ldg(b + sym(k, j) * S + o));
+            vl += Lv[lv] * (muq * __ldg(b + sym(l, j) * S + o));
+          }
+        }
+        q[0][d] = vj;
+        q[1][d] = vk;
+        q[2][d] = vl;
+      }
+      f[j] += ddiv(q[0][0], q[0][1], q[0][2], q[0][3], q[0][4], kd);
+      f[k] += ddiv(q[1][0], q[1][1], q[1][2], q[1][3], q[1][4], kd);
+      f[l] += ddiv(q[2][0], q[2][1], q[2][2], q[2][3], q[2][4], kd);
+    }
+    const float sf = inv_h / (g.rho * ca);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const int i0 = c * S + node, i1 = (9 + c) * S + node, i2 = (18 + c) * S + node;
+      const float u0 = __ldg(Y + i0), u1 = __ldg(Y + i1), u2 = __ldg(Y + i2);
+      const float acc = sf * f[c] - (cb * u2 + cc * u1 + cd * u0) * inv_a;
+      __stcs(a.out + (i0), stage_value(a, i0, u0, u1));
+      __stcs(a.out + (i1), stage_value(a, i1, u1, u2));
+      __stcs(a.out + (i2), stage_value(a, i2, u2, acc));
+    }
+  } else if (a.stage == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      __stcs(a.out + (c * S + node), 0.f);
+      __stcs(a.out + ((9 + c) * S + node), 0.f);
+      __stcs(a.out + ((18 + c) * S + node), 0.f);
+    }
+  }
+
+  // ---- stress rows
+  float H[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const int s = st[j], kd = kind[j];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+      H[i][j] = inv_h * (Le[j] * dav(Y + (18 + i) * S, node, s, kd) + Lp[j] * dav(Y + (9 + i) * S, node, s, kd) +
+                         Lw[j] * dav(Y + i * S, node, s, kd));
+  }
+  float src[6] = {H[0][0], H[1][1], H[2][2], H[1][2] + H[2][1], H[0][2] + H[2][0], H[0][1] + H[1][0]};
+  if (!ADJ) {
+    const float tr = src[0] + src[1] + src[2];
+#pragma unroll
+    for (int c = 0; c < 3; c++) src[c] = 2.f * mu * src[c] + lam * tr;
+#pragma unroll
+    for (int c = 3; c < 6; c++) src[c] = mu * src[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    const int i0 = (3 + c) * S + node, i1 = (12 + c) * S + node, i2 = (21 + c) * S + node;
+    const float s0 = __ldg(Y + i0), s1 = __ldg(Y + i1), s2 = __ldg(Y + i2);
+    __stcs(a.out + (i0), stage_value(a, i0, s0, s1));
+    __stcs(a.out + (i1), stage_value(a, i1, s1, s2));
+    __stcs(a.out + (i2), stage_value(a, i2, s2, (src[c] - cb * s2 - cc * s1 - cd * s0) * inv_a));
+  }
+}
+
+
+__device__ __forceinline__ int mat_at(const Geo &g, int I, int J, int K) {
+  int i = I - 2 * g.lo[0], j = J - 2 * g.lo[1], k = K - 2 * g.lo[2];
+  i = i < 0 ? 0 : (i >= g.m[0] ? g.m[0] - 1 : i);
+  j = j < 0 ? 0 : (j >= g.m[1] ? g.m[1] - 1 : j);
+  k = k < 0 ? 0 : (k >= g.m[2] ? g.m[2] - 1 : k);
+  return (k * g.m[1] + j) * g.m[0] + i;
+}
+
+// ---------------------------------------------------------------------------
+// Vectorised pair path: a thread owns the nodes (I0, I0 + 1), I0 even, of a bulk
+// row. Rows are padded to a multiple of 4 nodes, so every (I0, I0 + 1) pair is
+// 8-byte aligned: all loads and stores are float2 and fully coalesced.
+// x-window of a field: values at I0-2 .. I0+3; the even node's x kind is LR, the
+// odd node's C.
+__device__ __forceinline__ float2 ld2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ float2 ldcs2(const float *p) { return __ldcs(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ void st2(float *p, float a, float b, bool even_ok) {
+  if (even_ok)
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+  else
+    __stcs(p + 1, b);
+}
+
+struct XWin {
+  float v[6];
+};
+__device__ __forceinline__ XWin xwin(const float *p) {
+  const float2 a = ld2(p - 2), b = ld2(p), c = ld2(p + 2);
+  XWin w;
+  w.v[0] = a.x; w.v[1] = a.y; w.v[2] = b.x; w.v[3] = b.y; w.v[4] = c.x; w.v[5] = c.y;
+  return w;
+}
+// D_x (times h) of the even (LR) and odd (C) node
+__device__ __forceinline__ float dxe(const XWin &w) { return 0.5f * (w.v[0] - 4.f * w.v[1] + 4.f * w.v[3] - w.v[4]); }
+__device__ __forceinline__ float dxo(const XWin &w) { return w.v[4] - w.v[2]; }
+
+// derivative (times h) along y or z (stride s) of a field for both nodes
+template <int KD>
+__device__ __forceinline__ float2 dline(const float *p, int s) {
+  const float2 m1 = ld2(p - s), p1 = ld2(p + s);
+  if constexpr (KD == kSC) {
+    return make_float2(p1.x - m1.x, p1.y - m1.y);
+  } else {
+    const float2 m2 = ld2(p - 2 * s), p2 = ld2(p + 2 * s);
+    return make_float2(0.5f * (m2.x - 4.f * m1.x + 4.f * p1.x - p2.x), 0.5f * (m2.y - 4.f * m1.y + 4.f * p1.y - p2.y));
+  }
+}
+
+struct Coef {
+  float ca, cb, cc, cd, Le[3], Lp[3], Lw[3];
+};
+__device__ __forceinline__ Coef coef_at(const Geo &g, int I, int J, int K) {
+  const float alx = __ldg(g.alpha[0] + I), aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
+  const float bex = __ldg(g.beta[0] + I), bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
+  Coef c;
+  c.ca = alx * aly * alz;
+  c.cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
+  c.cc = alx * bey * bez + bex * aly * bez + bex * bey * alz;
+  c.cd = bex * bey * bez;
+  c.Le[0] = aly * alz; c.Le[1] = alx * alz; c.Le[2] = alx * aly;
+  c.Lp[0] = aly * bez + bey * alz; c.Lp[1] = alx * bez + bex * alz; c.Lp[2] = alx * bey + bex * aly;
+  c.Lw[0] = bey * bez; c.Lw[1] = bex * bez; c.Lw[2] = bex * bey;
+  return c;
+}
+__device__ __forceinline__ float lam_of(const Coef &c, int lv, int j) { return lv == 0 ? c.Lw[j] : (lv == 1 ? c.Lp[j] : c.Le[j]); }
+
+__device__ __forceinline__ float2 stage2(const StageArgs &a, int idx, float y0, float y1, float r0, float r1) {
+  if (a.stage == 0) return make_float2(r0, r1);
+  const float2 x = ldcs2(a.X + idx);
+  if (a.stage < 4) return make_float2(x.x + a.cdt * r0, x.y + a.cdt * r1);
+  const float2 b = ldcs2(a.Y2 + idx), c = ldcs2(a.Y3 + idx);
+  return make_float2((-x.x + b.x + 2.f * c.x + y0) * (1.f / 3.f) + a.cdt * r0,
+                     (-x.y + b.y + 2.f * c.y + y1) * (1.f / 3.f) + a.cdt * r1);
+}
+
+// adjoint: column j of sum_lv Lambda^lv_jj tau(T^lv) at node (I, J, K) for the node
+// whose Lambda_jj is Lj[] (levels 0..2), T read at offset o
+template <int JAX>
+__device__ __forceinline__ float3 tau_col(const Geo &g, const float *__restrict__ Y, int S, int o, int I, int J, int K,
+                                          const float Lj[3]) {
+  constexpr int KAX = (JAX + 1) % 3, LAX = (JAX + 2) % 3;
+  const int mq = mat_at(g, I, J, K);
+  const float lq = __ldg(g.lam + mq), muq = __ldg(g.mu + mq);
+  float qj = 0.f, qk = 0.f, ql = 0.f;
+#pragma unroll
+  for (int lv = 0; lv < 3; lv++) {
+    const float *b = Y + (9 * lv + 3) * S + o;
+    const float tjj = __ldg(b + JAX * S), tkk = __ldg(b + KAX * S), tll = __ldg(b + LAX * S);
+    qj += Lj[lv] * (2.f * muq * tjj + lq * (tjj + tkk + tll));
+    qk += Lj[lv] * (muq * __ldg(b + sym(KAX, JAX) * S));
+    ql += Lj[lv] * (muq * __ldg(b + sym(LAX, JAX) * S));
+  }
+  return make_float3(qj, qk, ql);
+}
+
+// adjoint: y- and z-line contributions sum_j D_j Q_cj for one node, as weighted
+// sums over the line points (C: q[+1] - q[-1]; LR: 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]))
+template <int KY, int KZ>
+__device__ __forceinline__ void adj_yz(const Geo &g, const float *__restrict__ Yn, int S, int sy, int sz, int I, int J,
+                                       int K, const Coef &cf, float f[3]) {
+  const float Ly[3] = {cf.Lw[1], cf.Lp[1], cf.Le[1]};
+#pragma unroll 1
+  for (int d = -2; d <= 2; d++) {
+    if (d == 0 || (KY == kSC && (d == -2 || d == 2))) continue;
+    const float w = KY == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f)));
+    const float3 q = tau_col<1>(g, Yn, S, d * sy, I, J + d, K, Ly);  // (yy, zy, xy) column
+    f[1] += w * q.x; f[2] += w * q.y; f[0] += w * q.z;
+  }
+  const float Lz[3] = {cf.Lw[2], cf.Lp[2], cf.Le[2]};
+#pragma unroll 1
+  for (int d = -2; d <= 2; d++) {
+    if (d == 0 || (KZ == kSC && (d == -2 || d == 2))) continue;
+    const float w = KZ == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f)));
+    const float3 q = tau_col<2>(g, Yn, S, d * sz, I, J, K + d, Lz);  // (zz, xz, yz) column
+    f[2] += w * q.x; f[0] += w * q.y; f[1] += w * q.z;
+  }
+}
+
+template <bool ADJ, int KY, int KZ>
+__device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K, bool even_ok) {
+  const int S = (int)g.stride;
+  const int node = (K * g.n[1] + J) * g.px + I0;
+  const int sy = g.px, sz = g.px * g.n[1];
+  const float *__restrict__ Yn = a.Y + node;
+  const Coef ce = coef_at(g, I0, J, K), co = coef_at(g, I0 + 1, J, K);
+  float fe[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};  // u-row sums (times h)
+  if constexpr (ADJ) {
+    // Q = sum_lv Lambda^lv_jj tau(T^lv): pointwise with the material of each line point
+    {  // x: points I0-2 .. I0+2 (Lambda_xx is the same for both nodes)
+      // even (LR) weights 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]); odd (C, at I0+1): q[+2] - q[0]
+      const float Lx[3] = {ce.Lw[0], ce.Lp[0], ce.Le[0]};
+#pragma unroll 1
+      for (int d = 0; d < 5; d++) {
+        const float we = d == 0 ? 0.5f : (d == 1 ? -2.f : (d == 3 ? 2.f : (d == 4 ? -0.5f : 0.f)));
+        const float wo = d == 2 ? -1.f : (d == 4 ? 1.f : 0.f);
+        const float3 q = tau_col<0>(g, Yn, S, d - 2, I0 + d - 2, J, K, Lx);
+        fe[0] += we * q.x; fe[1] += we * q.y; fe[2] += we * q.z;
+        fo[0] += wo * q.x; fo[1] += wo * q.y; fo[2] += wo * q.z;
+      }
+    }
+    adj_yz<KY, KZ>(g, Yn, S, sy, sz, I0, J, K, ce, fe);
+    adj_yz<KY, KZ>(g, Yn + 1, S, sy, sz, I0 + 1, J, K, co, fo);
+  }
+  // ---- S rows: H_ij = sum_lv Lambda^lv_jj D_j u^lv_i (times h); keep the own u values
+  float He[3][3], Ho[3][3], ue[3][3], uo[3][3];  // [i][j], [lv][i]
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) He[i][j] = Ho[i][j] = 0.f;
+#pragma unroll
+  for (int lv = 0; lv < 3; lv++)
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const float *p = Yn + (9 * lv + i) * S;
+      const XWin w = xwin(p);
+      const float2 dy = dline<KY>(p, sy), dz = dline<KZ>(p, sz);
+      ue[lv][i] = w.v[2];
+      uo[lv][i] = w.v[3];
+      He[i][0] += lam_of(ce, lv, 0) * dxe(w);
+      Ho[i][0] += lam_of(co, lv, 0) * dxo(w);
+      He[i][1] += lam_of(ce, lv, 1) * dy.x;
+      Ho[i][1] += lam_of(co, lv, 1) * dy.y;
+      He[i][2] += lam_of(ce, lv, 2) * dz.x;
+      Ho[i][2] += lam_of(co, lv, 2) * dz.y;
+    }
+  float se[6] = {He[0][0], He[1][1], He[2][2], He[1][2] + He[2][1], He[0][2] + He[2][0], He[0][1] + He[1][0]};
+  float so[6] = {Ho[0][0], Ho[1][1], Ho[2][2], Ho[1][2] + Ho[2][1], Ho[0][2] + Ho[2][0], Ho[0][1] + Ho[1][0]};
+  if constexpr (!ADJ) {  // tau(P(H)) with the node's own material
+    const int me = mat_at(g, I0, J, K), mo = mat_at(g, I0 + 1, J, K);
+    const float le = __ldg(g.lam + me), mue = __ldg(g.mu + me), lo = __ldg(g.lam + mo), muo = __ldg(g.mu + mo);
+    const float tre = se[0] + se[1] + se[2], tro = so[0] + so[1] + so[2];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      se[c] = 2.f * mue * se[c] + le * tre;
+      so[c] = 2.f * muo * so[c] + lo * tro;
+    }
+#pragma unroll
+    for (int c = 3; c < 6; c++) {
+      se[c] *= mue;
+      so[c] *= muo;
+    }
+  }
+
+  // ---- u rows (times h): f_c = sum_j D_j Q_cj; forward Q = sum_lv Lambda^lv_jj S^lv
+  const float inv_h = g.inv_h;
+  // S components in the order xx yy zz yz xz xy; for each: (c, j) pairs it feeds
+#pragma unroll
+  for (int comp = 0; comp < 6; comp++) {
+    float s0[3], s1[3];  // own values per level, even / odd
+#pragma unroll
+    for (int lv = 0; lv < 3; lv++) {
+      const float *p = Yn + (9 * lv + 3 + comp) * S;
+      const bool on_x = comp == 0 || comp == 4 || comp == 5;  // xx, xz, xy
+      const bool on_y = comp == 1 || comp == 3 || comp == 5;  // yy, yz, xy
+      const bool on_z = comp == 2 || comp == 3 || comp == 4;  // zz, yz, xz
+      if (on_x) {
+        const XWin w = xwin(p);
+        s0[lv] = w.v[2];
+        s1[lv] = w.v[3];
+        if constexpr (!ADJ) {
+          const int c = comp == 0 ? 0 : (comp == 5 ? 1 : 2);  // xx -> c 0, xy -> c 1, xz -> c 2 (j = x)
+          fe[c] += lam_of(ce, lv, 0) * dxe(w);
+          fo[c] += lam_of(co, lv, 0) * dxo(w);
+        }
+      } else {
+        const float2 v = ld2(p);
+        s0[lv] = v.x;
+        s1[lv] = v.y;
+      }
+      if constexpr (!ADJ) {
+        if (on_y) {
+          const float2 d = dline<KY>(p, sy);
+          const int c = comp == 1 ? 1 : (comp == 5 ? 0 : 2);  // yy -> 1, xy -> 0, yz -> 2 (j = y)
+          fe[c] += lam_of(ce, lv, 1) * d.x;
+          fo[c] += lam_of(co, lv, 1) * d.y;
+        }
+        if (on_z) {
+          const float2 d = dline<KZ>(p, sz);
+          const int c = comp == 2 ? 2 : (comp == 4 ? 0 : 1);  // zz -> 2, xz -> 0, yz -> 1 (j = z)
+          fe[c] += lam_of(ce, lv, 2) * d.x;
+          fo[c] += lam_of(co, lv, 2) * d.y;
+        }
+      }
+    }
+    // stress update of this component: S'' = (src - b S' - c S - d Sbar) / a
+    const int i0 = (3 + comp) * S + node, i1 = (12 + comp) * S + node, i2 = (21 + comp) * S + node;
+    const float ae = (se[comp] * inv_h - ce.cb * s0[2] - ce.cc * s0[1] - ce.cd * s0[0]) / ce.ca;
+    const float ao = (so[comp] * inv_h - co.cb * s1[2] - co.cc * s1[1] - co.cd * s1[0]) / co.ca;
+    float2 v;
+    v = stage2(a, i0, s0[0], s1[0], s0[1], s1[1]);
+    st2(a.out + i0, v.x, v.y, even_ok);
+    v = stage2(a, i1, s0[1], s1[1], s0[2], s1[2]);
+    st2(a.out + i1, v.x, v.y, even_ok);
+    v = stage2(a, i2, s0[2], s1[2], ae, ao);
+    st2(a.out + i2, v.x, v.y, even_ok);
+  }
+  // ---- displacement update: u'' = (f / h) / (rho a) - (b u' + c u + d ubar) / a
+  const float sfe = inv_h / (g.rho * ce.ca), sfo = inv_h / (g.rho * co.ca);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const int i0 = c * S + node, i1 = (9 + c) * S + node, i2 = (18 + c) * S + node;
+    const float ae = sfe * fe[c] - (ce.cb * ue[2][c] + ce.cc * ue[1][c] + ce.cd * ue[0][c]) / ce.ca;
+    const float ao = sfo * fo[c] - (co.cb * uo[2][c] + co.cc * uo[1][c] + co.cd * uo[0][c]) / co.ca;
+    float2 v;
+    v = stage2(a, i0, ue[0][c], uo[0][c], ue[1][c], uo[1][c]);
+    st2(a.out + i0, v.x, v.y, even_ok);
+    v = stage2(a, i1, ue[1][c], uo[1][c], ue[2][c], uo[2][c]);
+    st2(a.out + i1, v.x, v.y, even_ok);
+    v = stage2(a, i2, ue[2][c], uo[2][c], ae, ao);
+    st2(a.out + i2, v.x, v.y, even_ok);
+  }
+}
+
+#ifndef FWI_PML_BY
+#define FWI_PML_BY 4
+#endif
+#ifndef FWI_PML_MINB
+#define FWI_PML_MINB 6
+#endif
+#ifndef FWI_FACE_MINB
+#define FWI_FACE_MINB 1
+#endif
+constexpr int kBX = 32, kBY = FWI_PML_BY;
+
+// grid.x: blocks of kBY row tasks; a row task is one (J, K) row of one region box;
+// the 32 threads of a warp walk the row's node pairs. The boxes exclude the outer
+// faces of the grid, so every node takes the bulk path.
+template <bool ADJ>
+__global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, StageArgs a, Region r) {
+  const int task = blockIdx.x * kBY + threadIdx.y;
+  if (task >= r.rows_before[r.nbox]) return;
+  int b = 0;
+  while (b + 1 < r.nbox && task >= r.rows_before[b + 1]) b++;
+  const int t = task - r.rows_before[b];
+  // rows in plane-major order (J fastest): the blocks in flight cover a few
+  // consecutive planes, whose input state (the stencil operand) stays in L2 while
+  // the once-touched operands stream through with evict-first hints
+  const int ny = r.hi[b][1] - r.lo[b][1] + 1;
+  const int J = r.lo[b][1] + t % ny, K = r.lo[b][2] + t / ny;
+  const int x0 = r.lo[b][0] & ~1;  // pairs start at even x
+  const int ky = side_kind(J, g.n[1]), kz = side_kind(K, g.n[2]);
+  for (int I0 = x0 + 2 * threadIdx.x; I0 <= r.hi[b][0]; I0 += 2 * kBX) {
+    // box x-ranges start at odd nodes and end at odd nodes, so the odd node of a
+    // pair is always in the box; the even node may not be (its results are dropped)
+    const bool even_ok = I0 >= r.lo[b][0];
+    if (ky == kSC) {
+      if (kz == kSC) pml_pair<ADJ, kSC, kSC>(g, a, I0, J, K, even_ok);
+      else pml_pair<ADJ, kSC, kSLR>(g, a, I0, J, K, even_ok);
+    } else {
+      if (kz == kSC) pml_pair<ADJ, kSLR, kSC>(g, a, I0, J, K, even_ok);
+      else pml_pair<ADJ, kSLR, kSLR>(g, a, I0, J, K, even_ok);
+    }
+  }
+}
+
+// PML nodes on the outer faces of the grid (fixed faces, and the free top face
+// outside the interior), from a list built once per context: generic path
+template <bool ADJ>
+__global__ void __launch_bounds__(128, FWI_FACE_MINB) pml_face_kernel(Geo g, StageArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nface) return;
+  const int node = g.face[i];
+  const int I = node % g.px, rr = node / g.px;
+  pml_node<ADJ>(g, a, I, rr % g.n[1], rr / g.n[1]);
+}
+
+}  // namespace
+
+// boxes of the nodes outside the closed interior box [2lo, 2hi] (free top: from k = 0)
+static Region pml_region(const Geo &g) {
+  Region r{};
+  const int c0[3] = {2 * g.lo[0], 2 * g.lo[1], g.top_dir ? 2 * g.lo[2] : 0};
+  const int c1[3] = {2 * g.hi[0], 2 * g.hi[1], 2 * g.hi[2]};
+  auto add = [&](int x0, int x1, int y0, int y1, int z0, int z1) {
+    if (x0 > x1 || y0 > y1 || z0 > z1) return;
+    const int b = r.nbox++;
+    r.lo[b][0] = x0; r.hi[b][0] = x1;
+    r.lo[b][1] = y0; r.hi[b][1] = y1;
+    r.lo[b][2] = z0; r.hi[b][2] = z1;
+  };
+  // boxes clipped to the grid without its outer faces (those go to pml_face_kernel)
+  const int nx = g.n[0] - 2, ny = g.n[1] - 2, nz = g.n[2] - 2;
+  const int z0 = c0[2] > 1 ? c0[2] : 1, y0 = c0[1] > 1 ? c0[1] : 1;
+  add(1, nx, 1, ny, c1[2] + 1, nz);                       // below the interior
+  add(1, nx, 1, ny, 1, c0[2] - 1);                        // above (top PML)
+  add(1, nx, 1, c0[1] - 1, z0, c1[2]);                    // y- side
+  add(1, nx, c1[1] + 1, ny, z0, c1[2]);                   // y+ side
+  add(1, c0[0] - 1, y0, c1[1], z0, c1[2]);                // x- side
+  add(c1[0] + 1, nx, y0, c1[1], z0, c1[2]);               // x+ side
+  r.rows_before[0] = 0;
+  for (int b = 0; b < r.nbox; b++)
+    r.rows_before[b + 1] = r.rows_before[b] + (r.hi[b][1] - r.lo[b][1] + 1) * (r.hi[b][2] - r.lo[b][2] + 1);
+  for (int b = r.nbox; b < 6; b++) r.rows_before[b + 1] = r.rows_before[b];
+  return r;
+}
+
+void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
+  const Region r = pml_region(g);
+  const int rows = r.rows_before[r.nbox];
+  if (rows == 0) return;
+  const dim3 grd((rows + kBY - 1) / kBY), blk(kBX, kBY);
+  if (adjoint)
+    pml_kernel<true><<<grd, blk, 0, s>>>(g, a, r);
+  else
+    pml_kernel<false><<<grd, blk, 0, s>>>(g, a, r);
+}
+
+void launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
+  if (g.nface <= 0) return;
+  const int nb = (g.nface + 127) / 128;
+  if (adjoint)
+    pml_face_kernel<true><<<nb, 128, 0, s>>>(g, a);
+  else
+    pml_face_kernel<false><<<nb, 128, 0, s>>>(g, a);
+}
+
+}  // namespace fwi

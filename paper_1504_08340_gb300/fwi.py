@@ -117,11 +117,11 @@ class Context:
         st = self.lib.fwi_create(C.byref(self.cfg), C.byref(self.ptr))
         if st != 0:
             raise FWIError(st, "fwi_create failed")
-        dims = (C.c_int64 * 8)()
+        dims = (C.c_int64 * 9)()
         self._check(self.lib.fwi_get_dims(self.ptr, dims))
         self.nn = tuple(dims[0:3])
-        self.nnode, self.nmat, self.stride, self.nelem, self.npml_nodes = (
-            dims[3], dims[4], dims[5], dims[6], dims[7])
+        self.nnode, self.nmat, self.stride, self.nelem, self.npml_nodes, self.px = (
+            dims[3], dims[4], dims[5], dims[6], dims[7], dims[8])
         self.nsteps, self.dt = nsteps, dt
         self.nrec = 0
         self.nshots = 0
@@ -211,6 +211,13 @@ class Context:
         out = np.empty(self.mat_shape())
         self._check(self.lib.fwi_get_mass_tilde(self.ptr, out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
+
+    def state_index(self):
+        """Offsets, inside one field of the state layout, of the nodes in natural order
+        ((k * NJ + j) * NI + i): the layout pads every row to the pitch px."""
+        ni, nj, nk = self.nn
+        k, j, i = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
+        return ((k * nj + j) * self.px + i).ravel()
 
     def rhs(self, state, adjoint=False, out=None):
         """Right side of the first-order system; state/out: [27, stride] float32."""

@@ -30,21 +30,22 @@ def _as_f64_of_f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
-def to_gpu_layout(Y, stride):
-    """oracle [3][nnode][9] -> library [27][stride] (field 9*l + c)"""
-    out = np.zeros((27, stride), dtype=np.float32)
-    n = Y.shape[1]
+def to_gpu_layout(Y, ctx):
+    """oracle [3][nnode][9] -> library [27][stride] (field 9*l + c, pitched rows)"""
+    out = np.zeros((27, ctx.stride), dtype=np.float32)
+    idx = ctx.state_index()
     for l in range(3):
         for c in range(9):
-            out[9 * l + c, :n] = Y[l, :, c]
+            out[9 * l + c, idx] = Y[l, :, c]
     return out
 
 
-def from_gpu_layout(G, nnode):
-    Y = np.zeros((3, nnode, 9))
+def from_gpu_layout(G, ctx):
+    idx = ctx.state_index()
+    Y = np.zeros((3, idx.size, 9))
     for l in range(3):
         for c in range(9):
-            Y[l, :, c] = G[9 * l + c, :nnode]
+            Y[l, :, c] = G[9 * l + c, idx]
     return Y
 
 
@@ -91,7 +92,7 @@ def test_rhs_parity(oracle_mod, mesh, adjoint):
             D = np.ones(9)
             D[3:] = -1
             Z = np.stack([-Y[0] * D, Y[1] * D, -Y[2] * D])
-        out = from_gpu_layout(ctx.rhs(to_gpu_layout(Z, ctx.stride), adjoint=adjoint), o.nnode)
+        out = from_gpu_layout(ctx.rhs(to_gpu_layout(Z, ctx), adjoint=adjoint), ctx)
     ref = o.rhs(Y, adjoint=adjoint)
     if adjoint:
         D = np.ones(9)
@@ -203,7 +204,7 @@ def test_grf_64x64x32_full_size_sampled(oracle_mod):
     ref = o.rhs(Y)
     with _ctx(w) as ctx:
         ctx.set_material(lam, mu)
-        out = from_gpu_layout(ctx.rhs(to_gpu_layout(Y, ctx.stride)), o.nnode)
+        out = from_gpu_layout(ctx.rhs(to_gpu_layout(Y, ctx)), ctx)
     for l in range(3):
         for sl in (slice(0, 3), slice(3, 9)):
             assert rel_l2(out[l][:, sl], ref[l][:, sl]) < 2e-5
@@ -248,3 +249,24 @@ def test_error_paths():
         obs = np.zeros(ctx.trace_shape(1), dtype=np.float32)
         J = ctx.misfit(obs)
         assert np.isfinite(J) and J > 0
+
+
+def test_multi_shot_forward_and_gradient_sum(oracle_mod):
+    """Two shots in one call: traces are per shot, J and the gradients sum over shots."""
+    w = fi.tiny(nx=3, ny=3, nz=2, npml=2, nsteps=40, f0=30.0, nrec_side=3)
+    l0, m0 = (_f32(a) for a in fi.medium(w, "trial"))
+    src = np.array([[6, 6, 0], [8, 7, 0]], dtype=np.int64)
+    dirs = np.array([[0.0, 0.0, 1.0], [0.3, -0.2, 0.9]])
+    rec = w.receivers()
+    obs = fi.synthetic_traces(w.nsteps, len(rec), 7, 1e-9)
+    with _gpu_setup(w, l0, m0, src, dirs, rec, w.ricker()) as ctx:
+        both = ctx.forward(0, 2)
+        one = ctx.forward(1, 1)
+        assert np.array_equal(both[1], one[0])
+        obs2 = _f32(np.stack([obs, 0.5 * obs]))
+        J, gl, gm = ctx.adjoint_gradient(obs2, 0, 2)
+        J0, gl0, gm0 = ctx.adjoint_gradient(_f32(obs2[:1]), 0, 1)
+        J1, gl1, gm1 = ctx.adjoint_gradient(_f32(obs2[1:]), 1, 1)
+    assert J == pytest.approx(J0 + J1, rel=1e-12)
+    assert np.allclose(gl, gl0 + gl1, rtol=1e-12, atol=1e-12 * np.abs(gl).max())
+    assert np.allclose(gm, gm0 + gm1, rtol=1e-12, atol=1e-12 * np.abs(gm).max())
