@@ -54,10 +54,16 @@ __device__ __forceinline__ float ddiv(float g_m2, float g_m1, float g0, float g_
 
 __host__ __device__ constexpr int sym(int i, int j) { return i == j ? i : (i + j == 1 ? 5 : (i + j == 2 ? 4 : 3)); }
 
+// PML boxes and their warp tasks. A warp task is R rows of one plane with equal
+// y parity (J0, J0 + 2, ..., J0 + 2(R-1)), R = 32 / (node pairs per row) for narrow
+// boxes, else R = 1 (the warp walks the row in chunks of 32 pairs). The side kinds
+// along y and z are then uniform across the warp.
 struct Region {
   int nbox;
   int lo[6][3], hi[6][3];  // inclusive node boxes
-  int rows_before[7];      // prefix sums of rows (J, K pairs) per box
+  int P[6], R[6];          // node pairs per row, rows per warp task
+  int jfirst[6][2], nj[6][2], groups[6][2];  // per y-parity class: first J, row count, warp groups per plane
+  int tasks_before[7];     // prefix sums of warp tasks per box
 };
 
 __device__ __forceinline__ float stage_value(const StageArgs &a, int idx, float yv, float rate) {
@@ -468,26 +474,34 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
 #endif
 constexpr int kBX = 32, kBY = FWI_PML_BY;
 
-// grid.x: blocks of kBY row tasks; a row task is one (J, K) row of one region box;
-// the 32 threads of a warp walk the row's node pairs. The boxes exclude the outer
-// faces of the grid, so every node takes the bulk path.
+// grid.x: blocks of kBY warp tasks (see Region); tasks of a box run plane by plane.
+// The boxes exclude the outer faces of the grid, so every node takes the bulk path.
 template <bool ADJ>
 __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, StageArgs a, Region r) {
   const int task = blockIdx.x * kBY + threadIdx.y;
-  if (task >= r.rows_before[r.nbox]) return;
+  if (task >= r.tasks_before[r.nbox]) return;
   int b = 0;
-  while (b + 1 < r.nbox && task >= r.rows_before[b + 1]) b++;
-  const int t = task - r.rows_before[b];
-  // rows in plane-major order (J fastest): the blocks in flight cover a few
-  // consecutive planes, whose input state (the stencil operand) stays in L2 while
-  // the once-touched operands stream through with evict-first hints
-  const int ny = r.hi[b][1] - r.lo[b][1] + 1;
-  const int J = r.lo[b][1] + t % ny, K = r.lo[b][2] + t / ny;
+  while (b + 1 < r.nbox && task >= r.tasks_before[b + 1]) b++;
+  const int t = task - r.tasks_before[b];
+  const int G = r.groups[b][0] + r.groups[b][1];
+  const int K = r.lo[b][2] + t / G;
+  int q = t % G;
+  const int cls = q < r.groups[b][0] ? 0 : 1;
+  if (cls) q -= r.groups[b][0];
+  const int P = r.P[b], R = r.R[b];
   const int x0 = r.lo[b][0] & ~1;  // pairs start at even x
-  const int ky = side_kind(J, g.n[1]), kz = side_kind(K, g.n[2]);
-  for (int I0 = x0 + 2 * threadIdx.x; I0 <= r.hi[b][0]; I0 += 2 * kBX) {
-    // box x-ranges start at odd nodes and end at odd nodes, so the odd node of a
-    // pair is always in the box; the even node may not be (its results are dropped)
+  const int kz = side_kind(K, g.n[2]);
+  const int ky = side_kind(r.jfirst[b][cls], g.n[1]);
+  const int rr = R > 1 ? threadIdx.x / P : 0;   // row of the group handled by this lane
+  const int jrow = q * R + rr;
+  if (rr >= R || jrow >= r.nj[b][cls]) return;
+  const int J = r.jfirst[b][cls] + 2 * jrow;
+  const int p0 = R > 1 ? threadIdx.x % P : threadIdx.x;
+  const int pstep = R > 1 ? P : kBX;
+  for (int p = p0; p < P; p += pstep) {
+    const int I0 = x0 + 2 * p;
+    // box x-ranges start and end at odd nodes, so the odd node of a pair is always
+    // in the box; the even node may not be (its results are dropped)
     const bool even_ok = I0 >= r.lo[b][0];
     if (ky == kSC) {
       if (kz == kSC) pml_pair<ADJ, kSC, kSC>(g, a, I0, J, K, even_ok);
@@ -533,18 +547,29 @@ static Region pml_region(const Geo &g) {
   add(1, nx, c1[1] + 1, ny, z0, c1[2]);                   // y+ side
   add(1, c0[0] - 1, y0, c1[1], z0, c1[2]);                // x- side
   add(c1[0] + 1, nx, y0, c1[1], z0, c1[2]);               // x+ side
-  r.rows_before[0] = 0;
-  for (int b = 0; b < r.nbox; b++)
-    r.rows_before[b + 1] = r.rows_before[b] + (r.hi[b][1] - r.lo[b][1] + 1) * (r.hi[b][2] - r.lo[b][2] + 1);
-  for (int b = r.nbox; b < 6; b++) r.rows_before[b + 1] = r.rows_before[b];
+  r.tasks_before[0] = 0;
+  for (int b = 0; b < r.nbox; b++) {
+    r.P[b] = (r.hi[b][0] - (r.lo[b][0] & ~1)) / 2 + 1;
+    r.R[b] = r.P[b] >= 16 ? 1 : 32 / r.P[b];
+    int per_plane = 0;
+    for (int c = 0; c < 2; c++) {
+      const int jf = r.lo[b][1] + ((r.lo[b][1] & 1) != c ? 1 : 0);  // first J of parity c
+      r.jfirst[b][c] = jf;
+      r.nj[b][c] = jf > r.hi[b][1] ? 0 : (r.hi[b][1] - jf) / 2 + 1;
+      r.groups[b][c] = (r.nj[b][c] + r.R[b] - 1) / r.R[b];
+      per_plane += r.groups[b][c];
+    }
+    r.tasks_before[b + 1] = r.tasks_before[b] + per_plane * (r.hi[b][2] - r.lo[b][2] + 1);
+  }
+  for (int b = r.nbox; b < 6; b++) r.tasks_before[b + 1] = r.tasks_before[b];
   return r;
 }
 
 void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
   const Region r = pml_region(g);
-  const int rows = r.rows_before[r.nbox];
-  if (rows == 0) return;
-  const dim3 grd((rows + kBY - 1) / kBY), blk(kBX, kBY);
+  const int tasks = r.tasks_before[r.nbox];
+  if (tasks == 0) return;
+  const dim3 grd((tasks + kBY - 1) / kBY), blk(kBX, kBY);
   if (adjoint)
     pml_kernel<true><<<grd, blk, 0, s>>>(g, a, r);
   else
