@@ -225,6 +225,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inversion-steps", type=int, default=2,
+                    help="iterations of Algorithm 2 (fwi_step) timed after the gradient benchmark (0: skip)")
     ap.add_argument("--profile-forward", type=int, default=0, metavar="NSTEPS",
                     help="profiling aid: run only short forward sweeps (NSTEPS RK4 steps) on the same mesh")
     args = ap.parse_args()
@@ -313,6 +315,23 @@ def main():
                "d2h_bytes_per_step": int(gln.nbytes + gmn.nbytes + 8)}
         assert abs(Je - J) <= 1e-12 * abs(J)
 
+    misfit_drop = None
+    if args.inversion_steps > 0:
+        # misfit drop per second of the full inversion iteration (gradient, L-BFGS direction,
+        # Armijo line search, update), from the trial model
+        ctx.set_material(torch.tensor(l0, device=dev), torch.tensor(m0, device=dev))
+        ctx.step_reset()
+        barrier()
+        t0 = time.perf_counter()
+        infos = [ctx.step(obs, first_step=0.05) for _ in range(args.inversion_steps)]
+        barrier()
+        sec = time.perf_counter() - t0
+        J_start, J_end = infos[0].J_old, infos[-1].J_new
+        misfit_drop = {"iterations": args.inversion_steps, "J_start": J_start, "J_end": J_end, "seconds": sec,
+                       "misfit_drop_per_s": (J_start - J_end) / sec,
+                       "log10_misfit_reduction_per_s": float(np.log10(J_start / J_end)) / sec if J_end > 0 else None,
+                       "line_search_trials": [i.trials for i in infos]}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -335,6 +354,7 @@ def main():
             "gpu_launches": int(all_launches),
             "clocks": clocks,
             "e2e": e2e,
+            "misfit_drop": misfit_drop,
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)

@@ -147,6 +147,47 @@ fwi_status fwi_misfit(fwi_ctx *ctx, int shot0, int nshots, const float *observed
 fwi_status fwi_adjoint_gradient(fwi_ctx *ctx, int shot0, int nshots, const float *observed,
                                 int on_device, double *J, double *g_lambda, double *g_mu);
 
+/* Options of one inversion iteration (fwi_step). */
+typedef struct {
+  int shot0, nshots;  /* shots whose summed misfit is minimised */
+  int invert;         /* 1: lambda only, 2: mu only, 3: both (simultaneous inversion) */
+  int lbfgs_m;        /* L-BFGS pairs kept (Sec. 3.2 keeps 15); 0: steepest descent */
+  double c1;          /* Armijo sufficient-decrease constant (Algorithm 1: 1e-4) */
+  double rho;         /* backtracking factor (Algorithm 1: 0.5) */
+  int max_backtracks; /* trial steps before the iteration gives up */
+  double first_step;  /* first trial update (no L-BFGS pairs yet): max|alpha d| = first_step * max|m| */
+} fwi_step_opts;
+
+typedef struct {
+  double J_old, J_new; /* misfit before and after the iteration */
+  double alpha;        /* accepted step length (alpha^lambda = alpha^mu, Algorithm 1) */
+  double gtd;          /* directional derivative of J along the search direction */
+  int trials;          /* misfit evaluations of the line search */
+  int accepted;        /* 1 when the Armijo condition held and the material moved */
+  int pairs;           /* L-BFGS pairs held after the iteration */
+} fwi_step_info;
+
+/* One iteration of Algorithm 2 (lines 6-11) at the current material:
+ * gradient (state (6), adjoint (15), g = Mtilde^-1 g_mis of (18) with R = 0),
+ * L-BFGS search direction (two-loop recursion in the Mtilde inner product,
+ * <a, b> = sum_i a_i Mtilde_i b_i, so that <g, d> = g_mis . d is the exact
+ * directional derivative), Armijo backtracking of Algorithm 1 (alpha^lambda =
+ * alpha^mu, halved together) and the update (19), which becomes the context's
+ * material. Trial materials that violate mu > 0, lambda + 2 mu > 0 or the time-step
+ * limit count as failed trials. The L-BFGS pairs live on the device (FP64, 2 *
+ * lbfgs_m vectors of 2 * dims[4] values) and persist between calls; a pair is kept
+ * only when <s, y> > 0. observed: as fwi_misfit (host or device); info: host.
+ * When no trial satisfies Armijo the material is restored, info->accepted = 0 and
+ * the memory is cleared. Errors: as fwi_adjoint_gradient, FWI_E_INVAL (options). */
+fwi_status fwi_step(fwi_ctx *ctx, const float *observed, int on_device, const fwi_step_opts *opts,
+                    fwi_step_info *info);
+
+/* Forget the L-BFGS pairs (e.g. when the source wavelet changes, Sec. 3.3.2). */
+fwi_status fwi_step_reset(fwi_ctx *ctx);
+
+/* Current material ([k][j][i] as in fwi_set_material; host or device). */
+fwi_status fwi_get_material(fwi_ctx *ctx, float *lambda, float *mu, int on_device);
+
 /* Diagonal of the lumped mass-like matrix Mtilde of (C.1a), FP64, on the
  * interior nodes (host array of dims[4] values). */
 fwi_status fwi_get_mass_tilde(fwi_ctx *ctx, double *mtilde);

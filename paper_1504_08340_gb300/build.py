@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libfwi.so")
-SOURCES = ["fwi_api.cu", "fwi_kernels.cu", "fwi_stage.cu", "fwi_interior.cu", "fwi_pml.cu", "fwi_noalloc.cu"]
+SOURCES = ["fwi_api.cu", "fwi_kernels.cu", "fwi_stage.cu", "fwi_interior.cu", "fwi_pml.cu", "fwi_opt.cu", "fwi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

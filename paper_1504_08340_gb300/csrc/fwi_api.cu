@@ -58,6 +58,15 @@ struct fwi_ctx {
   float *d_hist = nullptr;
   double *d_gl = nullptr, *d_gm = nullptr;
 
+  // reduced-space update (fwi_step): model, gradient, direction, L-BFGS pairs (FP64)
+  int lb_cap = 0, lb_count = 0, lb_head = 0;
+  bool lb_have_prev = false;
+  std::vector<double> lb_rho;
+  double *d_mt = nullptr, *d_m = nullptr, *d_mprev = nullptr, *d_g = nullptr, *d_gprev = nullptr;
+  double *d_dir = nullptr, *d_S = nullptr, *d_Yv = nullptr, *d_opart = nullptr, *d_oscal = nullptr;
+  unsigned *d_oflags = nullptr;
+  unsigned long long *d_omax = nullptr;
+
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
@@ -588,6 +597,11 @@ void fwi_destroy(fwi_ctx *c) {
   dfree(c->d_hist);
   dfree(c->d_gl);
   dfree(c->d_gm);
+  for (double **p : {&c->d_mt, &c->d_m, &c->d_mprev, &c->d_g, &c->d_gprev, &c->d_dir, &c->d_S, &c->d_Yv,
+                     &c->d_opart, &c->d_oscal})
+    dfree(*p);
+  dfree(c->d_oflags);
+  dfree(c->d_omax);
   for (int i = 0; i < 2; i++) {
     if (c->side[i]) {
       cudaStreamSynchronize(c->side[i]);
@@ -755,10 +769,10 @@ fwi_status fwi_forward(fwi_ctx *c, int shot0, int nshots, float *traces, int on_
   return FWI_OK;
 }
 
-fwi_status fwi_misfit(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device, double *J) {
-  if (!c) return FWI_E_INVAL;
-  TRY(require_ready(c, shot0, nshots));
-  if (!observed || !J) return fail(c, FWI_E_INVAL, "null argument");
+namespace {
+
+// misfit (7) of shots [shot0, shot0 + nshots) at the current material
+fwi_status run_misfit(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device, double *J) {
   TRY(ensure_trace_buffers(c));
   TRY(ensure_J(c, nshots));
   CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
@@ -772,11 +786,8 @@ fwi_status fwi_misfit(fwi_ctx *c, int shot0, int nshots, const float *observed, 
   return finish_J(c, nshots, J);
 }
 
-fwi_status fwi_adjoint_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device,
-                                double *J, double *g_lambda, double *g_mu) {
-  if (!c) return FWI_E_INVAL;
-  TRY(require_ready(c, shot0, nshots));
-  if (!observed || !g_lambda || !g_mu) return fail(c, FWI_E_INVAL, "null argument");
+// misfit and g_mis (dJ/dlambda_i, dJ/dmu_i) into d_gl / d_gm
+fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device, double *J) {
   TRY(ensure_trace_buffers(c));
   TRY(ensure_J(c, nshots));
   const size_t nmat = (size_t)c->geo.nmat;
@@ -814,14 +825,219 @@ fwi_status fwi_adjoint_gradient(fwi_ctx *c, int shot0, int nshots, const float *
   fwi::launch_check_finite(c->d_gl, (int64_t)nmat, c->d_flag, c->stream);
   fwi::launch_check_finite(c->d_gm, (int64_t)nmat, c->d_flag, c->stream);
   c->t_launch[3] += 2;
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  // stage the outputs only after the finite check: copy into the caller's arrays last
+  return finish_J(c, nshots, J);
+}
+
+}  // namespace
+
+fwi_status fwi_misfit(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device, double *J) {
+  if (!c) return FWI_E_INVAL;
+  TRY(require_ready(c, shot0, nshots));
+  if (!observed || !J) return fail(c, FWI_E_INVAL, "null argument");
+  return run_misfit(c, shot0, nshots, observed, on_device, J);
+}
+
+fwi_status fwi_adjoint_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device,
+                                double *J, double *g_lambda, double *g_mu) {
+  if (!c) return FWI_E_INVAL;
+  TRY(require_ready(c, shot0, nshots));
+  if (!observed || !g_lambda || !g_mu) return fail(c, FWI_E_INVAL, "null argument");
   double Jv = 0.0;
-  TRY(finish_J(c, nshots, &Jv));
+  TRY(run_gradient(c, shot0, nshots, observed, on_device, &Jv));
+  // the outputs are written only after the finite check in run_gradient passed
+  const size_t nmat = (size_t)c->geo.nmat;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   CUDA_TRY(c, cudaMemcpyAsync(g_lambda, c->d_gl, sizeof(double) * nmat, kind, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(g_mu, c->d_gm, sizeof(double) * nmat, kind, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (J) *J = Jv;
+  return FWI_OK;
+}
+
+
+namespace {
+
+// <a, b> in the Mtilde inner product over both halves, returned on the host
+fwi_status wdot(fwi_ctx *c, const double *a, const double *b, double *out) {
+  fwi::opt_wdot(a, b, c->d_mt, c->geo.nmat, c->d_opart, c->d_oscal, c->stream);
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->d_oscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
+fwi_status absmax(fwi_ctx *c, const double *x, double *out) {
+  CUDA_TRY(c, cudaMemsetAsync(c->d_omax, 0, sizeof(unsigned long long), c->stream));
+  fwi::opt_absmax(x, 2 * c->geo.nmat, c->d_omax, c->stream);
+  unsigned long long bits = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&bits, c->d_omax, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::memcpy(out, &bits, sizeof(double));
+  return FWI_OK;
+}
+
+// material m + alpha d into the context; *ok = 0 when it is inadmissible
+fwi_status set_trial(fwi_ctx *c, double alpha, const double *d, int *ok) {
+  CUDA_TRY(c, cudaMemsetAsync(c->d_oflags, 0, 2 * sizeof(unsigned), c->stream));
+  fwi::opt_trial(c->d_m, d, alpha, c->d_lam, c->d_mu, c->geo.nmat, c->d_oflags, c->stream);
+  unsigned fl[2] = {0, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(fl, c->d_oflags, sizeof fl, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  float pmax;
+  std::memcpy(&pmax, &fl[1], sizeof pmax);
+  const double cfl = c->cfg.dt * std::sqrt((double)pmax / c->cfg.rho) / (0.5 * c->cfg.h);
+  *ok = (fl[0] == 0 && cfl <= 0.66) ? 1 : 0;
+  return FWI_OK;
+}
+
+}  // namespace
+
+fwi_status fwi_step_reset(fwi_ctx *c) {
+  if (!c) return FWI_E_INVAL;
+  c->lb_count = c->lb_head = 0;
+  c->lb_have_prev = false;
+  return FWI_OK;
+}
+
+fwi_status fwi_get_material(fwi_ctx *c, float *lambda, float *mu, int on_device) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (!c->have_material) return fail(c, FWI_E_STATE, "material not set");
+  if (!lambda || !mu) return fail(c, FWI_E_INVAL, "null argument");
+  const size_t n = (size_t)c->geo.nmat;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(c, cudaMemcpyAsync(lambda, c->d_lam, n * sizeof(float), kind, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(mu, c->d_mu, n * sizeof(float), kind, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
+fwi_status fwi_step(fwi_ctx *c, const float *observed, int on_device, const fwi_step_opts *o, fwi_step_info *info) {
+  if (!c) return FWI_E_INVAL;
+  if (!o || !observed || !info) return fail(c, FWI_E_INVAL, "null argument");
+  TRY(require_ready(c, o->shot0, o->nshots));
+  if (o->invert < 1 || o->invert > 3 || o->lbfgs_m < 0 || o->lbfgs_m > 1000 || !(o->c1 > 0 && o->c1 < 1) ||
+      !(o->rho > 0 && o->rho < 1) || o->max_backtracks < 1 || !(o->first_step > 0))
+    return fail(c, FWI_E_INVAL, "invalid step options");
+  const int64_t nmat = c->geo.nmat, n2 = 2 * nmat;
+  // device vectors (allocated once; the pair store grows with lbfgs_m)
+  if (!c->d_mt) {
+    TRY(dalloc(c, &c->d_mt, (size_t)nmat));
+    std::vector<double> mt(nmat);
+    TRY(fwi_get_mass_tilde(c, mt.data()));
+    CUDA_TRY(c, cudaMemcpy(c->d_mt, mt.data(), sizeof(double) * nmat, cudaMemcpyHostToDevice));
+  }
+  for (double **p : {&c->d_m, &c->d_mprev, &c->d_g, &c->d_gprev, &c->d_dir}) TRY(dalloc(c, p, (size_t)n2));
+  TRY(dalloc(c, &c->d_opart, 1024));
+  TRY(dalloc(c, &c->d_oscal, 1));
+  TRY(dalloc(c, &c->d_oflags, 2));
+  TRY(dalloc(c, &c->d_omax, 1));
+  if (o->lbfgs_m != c->lb_cap) {
+    dfree(c->d_S);
+    dfree(c->d_Yv);
+    c->lb_cap = o->lbfgs_m;
+    c->lb_rho.assign(c->lb_cap, 0.0);
+    c->lb_count = c->lb_head = 0;
+    if (c->lb_cap > 0) {
+      TRY(dalloc(c, &c->d_S, (size_t)n2 * c->lb_cap));
+      TRY(dalloc(c, &c->d_Yv, (size_t)n2 * c->lb_cap));
+    }
+  }
+  // 1. misfit and gradient at the current material (Algorithm 2, lines 6-8)
+  double J0 = 0.0;
+  TRY(run_gradient(c, o->shot0, o->nshots, observed, on_device, &J0));
+  fwi::opt_pack(c->d_lam, c->d_mu, c->d_m, nmat, c->stream);
+  fwi::opt_riesz(c->d_gl, c->d_gm, c->d_mt, c->d_g, nmat, o->invert, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  // 2. new L-BFGS pair s = m_k - m_{k-1}, y = g_k - g_{k-1}, kept when <s, y> > 0
+  if (c->lb_have_prev && c->lb_cap > 0) {
+    double *S = c->d_S + (size_t)c->lb_head * n2, *Yv = c->d_Yv + (size_t)c->lb_head * n2;
+    CUDA_TRY(c, cudaMemcpyAsync(S, c->d_m, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    fwi::opt_axpby(S, -1.0, c->d_mprev, 1.0, n2, c->stream);
+    CUDA_TRY(c, cudaMemcpyAsync(Yv, c->d_g, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    fwi::opt_axpby(Yv, -1.0, c->d_gprev, 1.0, n2, c->stream);
+    double sy = 0.0;
+    TRY(wdot(c, S, Yv, &sy));
+    if (sy > 0.0 && std::isfinite(sy)) {
+      c->lb_rho[c->lb_head] = 1.0 / sy;
+      c->lb_head = (c->lb_head + 1) % c->lb_cap;
+      c->lb_count = std::min(c->lb_count + 1, c->lb_cap);
+    }
+  }
+  // 3. search direction: two-loop recursion, d = -H g
+  double gtd = 0.0;
+  for (int attempt = 0; attempt < 2; attempt++) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_dir, c->d_g, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    std::vector<double> al(c->lb_count);
+    for (int t = 0; t < c->lb_count; t++) {  // newest to oldest
+      const int i = (c->lb_head - 1 - t + c->lb_cap) % c->lb_cap;
+      double sq = 0.0;
+      TRY(wdot(c, c->d_S + (size_t)i * n2, c->d_dir, &sq));
+      al[t] = c->lb_rho[i] * sq;
+      fwi::opt_axpby(c->d_dir, -al[t], c->d_Yv + (size_t)i * n2, 1.0, n2, c->stream);
+    }
+    if (c->lb_count > 0) {  // H0 = <s, y> / <y, y> of the newest pair
+      const int i = (c->lb_head - 1 + c->lb_cap) % c->lb_cap;
+      double yy = 0.0;
+      TRY(wdot(c, c->d_Yv + (size_t)i * n2, c->d_Yv + (size_t)i * n2, &yy));
+      const double gamma = (1.0 / c->lb_rho[i]) / yy;
+      fwi::opt_axpby(c->d_dir, 0.0, c->d_dir, gamma, n2, c->stream);
+      for (int t = c->lb_count - 1; t >= 0; t--) {  // oldest to newest
+        const int j = (c->lb_head - 1 - t + c->lb_cap) % c->lb_cap;
+        double yr = 0.0;
+        TRY(wdot(c, c->d_Yv + (size_t)j * n2, c->d_dir, &yr));
+        const double beta = c->lb_rho[j] * yr;
+        fwi::opt_axpby(c->d_dir, al[t] - beta, c->d_S + (size_t)j * n2, 1.0, n2, c->stream);
+      }
+    } else {  // no curvature yet: steepest descent sized to first_step * max|m|
+      double gmax = 0.0, mmax = 0.0;
+      TRY(absmax(c, c->d_g, &gmax));
+      TRY(absmax(c, c->d_m, &mmax));
+      if (!(gmax > 0.0)) return fail(c, FWI_E_NONFINITE, "zero or non-finite gradient");
+      fwi::opt_axpby(c->d_dir, 0.0, c->d_dir, o->first_step * mmax / gmax, n2, c->stream);
+    }
+    fwi::opt_axpby(c->d_dir, 0.0, c->d_dir, -1.0, n2, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    TRY(wdot(c, c->d_g, c->d_dir, &gtd));
+    if (gtd < 0.0 && std::isfinite(gtd)) break;
+    c->lb_count = c->lb_head = 0;  // not a descent direction: drop the memory, steepest descent
+    if (attempt == 1) return fail(c, FWI_E_NONFINITE, "no descent direction");
+  }
+  // 4. Armijo backtracking (Algorithm 1) and update (19)
+  double alpha = 1.0, J1 = J0;
+  int trials = 0, accepted = 0;
+  for (int b = 0; b <= o->max_backtracks; b++, alpha *= o->rho) {
+    int ok = 0;
+    TRY(set_trial(c, alpha, c->d_dir, &ok));
+    if (!ok) continue;
+    double Jt = 0.0;
+    trials++;
+    fwi_status st = run_misfit(c, o->shot0, o->nshots, observed, on_device, &Jt);
+    if (st == FWI_E_NONFINITE) continue;
+    TRY(st);
+    if (Jt < J0 + o->c1 * alpha * gtd) {
+      J1 = Jt;
+      accepted = 1;
+      break;
+    }
+  }
+  if (!accepted) {  // restore the material and forget the curvature pairs
+    int ok = 0;
+    TRY(set_trial(c, 0.0, c->d_dir, &ok));
+    c->lb_count = c->lb_head = 0;
+    c->lb_have_prev = false;
+  } else {
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_mprev, c->d_m, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_gprev, c->d_g, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->stream));
+    c->lb_have_prev = true;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  info->J_old = J0;
+  info->J_new = J1;
+  info->alpha = accepted ? alpha : 0.0;
+  info->gtd = gtd;
+  info->trials = trials;
+  info->accepted = accepted;
+  info->pairs = c->lb_count;
   return FWI_OK;
 }
 

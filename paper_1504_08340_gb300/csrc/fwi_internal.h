@@ -95,4 +95,15 @@ void launch_sum(const double *part, int nblocks, double *out, cudaStream_t s);
 // flag = 1 if any value of x (n doubles) is not finite.
 void launch_check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);
 
+// reduced-space update helpers (fwi_opt.cu); vectors hold (lambda, mu) halves of nmat values
+void opt_wdot(const double *a, const double *b, const double *w, int64_t nmat, double *part, double *out,
+              cudaStream_t s);
+void opt_axpby(double *y, double a, const double *x, double b, int64_t n, cudaStream_t s);
+void opt_riesz(const double *gl, const double *gm, const double *mt, double *g, int64_t nmat, int mask,
+               cudaStream_t s);
+void opt_trial(const double *m, const double *d, double alpha, float *lam, float *mu, int64_t nmat, unsigned *flags,
+               cudaStream_t s);
+void opt_pack(const float *lam, const float *mu, double *m, int64_t nmat, cudaStream_t s);
+void opt_absmax(const double *x, int64_t n, unsigned long long *out, cudaStream_t s);
+
 }  // namespace fwi

@@ -33,11 +33,24 @@ class _Config(C.Structure):
                 ("dt", C.c_double), ("nsteps", C.c_int), ("cuda_stream", C.c_void_p)]
 
 
+class StepOpts(C.Structure):
+    """fwi_step_opts: one iteration of Algorithm 2 (L-BFGS + Armijo backtracking)."""
+    _fields_ = [("shot0", C.c_int), ("nshots", C.c_int), ("invert", C.c_int), ("lbfgs_m", C.c_int),
+                ("c1", C.c_double), ("rho", C.c_double), ("max_backtracks", C.c_int),
+                ("first_step", C.c_double)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("J_old", C.c_double), ("J_new", C.c_double), ("alpha", C.c_double), ("gtd", C.c_double),
+                ("trials", C.c_int), ("accepted", C.c_int), ("pairs", C.c_int)]
+
+
 # every symbol the header declares; the CPU test checks the library exports them all
 EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_get_dims",
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
-           "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc")
+           "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
+           "fwi_step_reset", "fwi_get_material")
 
 _lib = None
 
@@ -73,6 +86,9 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_get_timing.argtypes = [P, I, D, I64]
     lib.fwi_reset_timing.argtypes = [P]
     lib.fwi_trace_misfit_noalloc.argtypes = [P, P, I, I, C.c_double, P, D]
+    lib.fwi_step.argtypes = [P, P, I, C.POINTER(StepOpts), C.POINTER(StepInfo)]
+    lib.fwi_step_reset.argtypes = [P]
+    lib.fwi_get_material.argtypes = [P, P, P, I]
     for name in EXPORTS:
         if name not in ("fwi_destroy", "fwi_last_error", "fwi_status_string"):
             getattr(lib, name).restype = I
@@ -206,6 +222,24 @@ class Context:
         J = C.c_double()
         self._check(self.lib.fwi_adjoint_gradient(self.ptr, shot0, nshots, p, dev, C.byref(J), pl, pm))
         return J.value, g_lambda, g_mu
+
+    def step(self, observed, shot0=0, nshots=1, invert=3, lbfgs_m=15, c1=1e-4, rho=0.5, max_backtracks=20,
+             first_step=0.05):
+        """One iteration of Algorithm 2; returns the StepInfo (J_old, J_new, alpha, ...)."""
+        p, dev = _ptr(observed, np.float32)
+        opts = StepOpts(shot0, nshots, invert, lbfgs_m, c1, rho, max_backtracks, first_step)
+        info = StepInfo()
+        self._check(self.lib.fwi_step(self.ptr, p, dev, C.byref(opts), C.byref(info)))
+        return info
+
+    def step_reset(self):
+        self._check(self.lib.fwi_step_reset(self.ptr))
+
+    def get_material(self):
+        lam = np.empty(self.mat_shape(), dtype=np.float32)
+        mu = np.empty(self.mat_shape(), dtype=np.float32)
+        self._check(self.lib.fwi_get_material(self.ptr, C.c_void_p(lam.ctypes.data), C.c_void_p(mu.ctypes.data), 0))
+        return lam, mu
 
     def mass_tilde(self):
         out = np.empty(self.mat_shape())
