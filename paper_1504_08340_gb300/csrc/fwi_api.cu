@@ -32,6 +32,7 @@ struct fwi_ctx {
   float *state[4] = {nullptr, nullptr, nullptr, nullptr};  // X, Y2, Y3, Y4
   float *d_alpha[3] = {nullptr, nullptr, nullptr};
   float *d_beta[3] = {nullptr, nullptr, nullptr};
+  float *d_ialpha[3] = {nullptr, nullptr, nullptr};
   std::vector<double> h_alpha[3], h_beta[3];
   float *d_lam = nullptr, *d_mu = nullptr;
   int *d_shell = nullptr, *d_face = nullptr;
@@ -440,6 +441,7 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   g.stride = (px * nJ * nK + 63) / 64 * 64;
   g.inv_h = (float)(1.0 / cfg->h);
   g.rho = (float)cfg->rho;
+  g.inv_rho_h = (float)(1.0 / (cfg->rho * cfg->h));
   g.wdetj = (float)(0.125 * cfg->h * cfg->h * cfg->h);
   c->nelem = (int64_t)(nI / 2) * (nJ / 2) * (nK / 2);
   {
@@ -489,17 +491,21 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   for (int ax = 0; ax < 3 && st == FWI_OK; ax++) {
     st = dalloc(c, &c->d_alpha[ax], g.n[ax]);
     if (st == FWI_OK) st = dalloc(c, &c->d_beta[ax], g.n[ax]);
+    if (st == FWI_OK) st = dalloc(c, &c->d_ialpha[ax], g.n[ax]);
     if (st != FWI_OK) break;
-    std::vector<float> fa(g.n[ax]), fb(g.n[ax]);
+    std::vector<float> fa(g.n[ax]), fb(g.n[ax]), fi(g.n[ax]);
     for (int i = 0; i < g.n[ax]; i++) {
       fa[i] = (float)c->h_alpha[ax][i];
       fb[i] = (float)c->h_beta[ax][i];
+      fi[i] = (float)(1.0 / c->h_alpha[ax][i]);
     }
     if (cudaMemcpy(c->d_alpha[ax], fa.data(), sizeof(float) * g.n[ax], cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->d_beta[ax], fb.data(), sizeof(float) * g.n[ax], cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(c->d_beta[ax], fb.data(), sizeof(float) * g.n[ax], cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_ialpha[ax], fi.data(), sizeof(float) * g.n[ax], cudaMemcpyHostToDevice) != cudaSuccess)
       st = fail(c, FWI_E_CUDA, "stretch table upload failed");
     g.alpha[ax] = c->d_alpha[ax];
     g.beta[ax] = c->d_beta[ax];
+    g.ialpha[ax] = c->d_ialpha[ax];
   }
   if (st == FWI_OK && fwi::prepare_interior() != cudaSuccess) st = fail(c, FWI_E_CUDA, "kernel attribute setup failed");
   if (st == FWI_OK) {
@@ -578,6 +584,7 @@ void fwi_destroy(fwi_ctx *c) {
   for (int ax = 0; ax < 3; ax++) {
     dfree(c->d_alpha[ax]);
     dfree(c->d_beta[ax]);
+    dfree(c->d_ialpha[ax]);
   }
   dfree(c->d_lam);
   dfree(c->d_mu);

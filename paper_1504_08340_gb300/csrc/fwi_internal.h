@@ -22,8 +22,10 @@ struct Geo {
   int64_t nnode, nmat;
   float inv_h;      // 1 / h
   float rho;
+  float inv_rho_h;  // 1 / (rho h)
   float wdetj;      // (h/2)^3
   const float *alpha[3];  // stretch alpha_s at each node coordinate, per axis
+  const float *ialpha[3]; // 1 / alpha_s (rounded from FP64)
   const float *beta[3];   // stretch beta_s, 1/s
   const float *lam, *mu;  // interior material grid [k][j][i]
   const int *shell;       // node numbers of the interface shell (see shell_kernel)

@@ -221,17 +221,43 @@ __device__ __forceinline__ int mat_at(const Geo &g, int I, int J, int K) {
 // ---------------------------------------------------------------------------
 // Vectorised pair path: a thread owns the nodes (I0, I0 + 1), I0 even, of a bulk
 // row. Rows are padded to a multiple of 4 nodes, so every (I0, I0 + 1) pair is
-// 8-byte aligned: all loads and stores are float2 and fully coalesced.
-// x-window of a field: values at I0-2 .. I0+3; the even node's x kind is LR, the
-// odd node's C.
+// 8-byte aligned: all loads and stores are float2 and fully coalesced, and the
+// arithmetic of the two nodes runs as packed f32x2 instructions (.x: the even
+// node, .y: the odd node). x-window of a field: values at I0-2 .. I0+3; the even
+// node's x kind is LR, the odd node's C.
 __device__ __forceinline__ float2 ld2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
 __device__ __forceinline__ float2 ldcs2(const float *p) { return __ldcs(reinterpret_cast<const float2 *>(p)); }
-__device__ __forceinline__ void st2(float *p, float a, float b, bool even_ok) {
+__device__ __forceinline__ void st2(float *p, float2 v, bool even_ok) {
   if (even_ok)
-    __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+    __stcs(reinterpret_cast<float2 *>(p), v);
   else
-    __stcs(p + 1, b);
+    __stcs(p + 1, v.y);
 }
+
+// packed two-lane FP32 arithmetic, round to nearest even (each lane as the scalar op)
+#define FWI_PACKED_BINARY(name, op)                                                                   \
+  __device__ __forceinline__ float2 name(float2 a, float2 b) {                                        \
+    float2 d;                                                                                         \
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" op        \
+        ".rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                          \
+        : "=f"(d.x), "=f"(d.y)                                                                        \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                                    \
+    return d;                                                                                         \
+  }
+FWI_PACKED_BINARY(padd, "add")
+FWI_PACKED_BINARY(psub, "sub")
+FWI_PACKED_BINARY(pmul, "mul")
+#undef FWI_PACKED_BINARY
+// a * b + c, one rounding per lane
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
 
 struct XWin {
   float v[6];
@@ -242,51 +268,60 @@ __device__ __forceinline__ XWin xwin(const float *p) {
   w.v[0] = a.x; w.v[1] = a.y; w.v[2] = b.x; w.v[3] = b.y; w.v[4] = c.x; w.v[5] = c.y;
   return w;
 }
-// D_x (times h) of the even (LR) and odd (C) node
-__device__ __forceinline__ float dxe(const XWin &w) { return 0.5f * (w.v[0] - 4.f * w.v[1] + 4.f * w.v[3] - w.v[4]); }
-__device__ __forceinline__ float dxo(const XWin &w) { return w.v[4] - w.v[2]; }
+// D_x (times h) of the even (LR) and the odd (C) node
+__device__ __forceinline__ float2 dx2(const XWin &w) {
+  return make_float2(0.5f * (w.v[0] - w.v[4]) + 2.f * (w.v[3] - w.v[1]), w.v[4] - w.v[2]);
+}
 
-// derivative (times h) along y or z (stride s) of a field for both nodes
+// derivative (times h) along y or z (stride s) of a field for both nodes:
+// C: v[+1] - v[-1]; LR: 2 (v[+1] - v[-1]) + 0.5 (v[-2] - v[+2])
 template <int KD>
 __device__ __forceinline__ float2 dline(const float *p, int s) {
   const float2 m1 = ld2(p - s), p1 = ld2(p + s);
   if constexpr (KD == kSC) {
-    return make_float2(p1.x - m1.x, p1.y - m1.y);
+    return psub(p1, m1);
   } else {
     const float2 m2 = ld2(p - 2 * s), p2 = ld2(p + 2 * s);
-    return make_float2(0.5f * (m2.x - 4.f * m1.x + 4.f * p1.x - p2.x), 0.5f * (m2.y - 4.f * m1.y + 4.f * p1.y - p2.y));
+    return pfma(bc(2.f), psub(p1, m1), pmul(bc(0.5f), psub(m2, p2)));
   }
 }
 
-struct Coef {
-  float ca, cb, cc, cd, Le[3], Lp[3], Lw[3];
+// stretch coefficients of a pair. Level order lv = 0, 1, 2: Lambda^w, Lambda^p, Lambda^e.
+// Lambda_xx does not depend on x, so it is one value for both nodes.
+struct Coef2 {
+  float2 ia, nb, nc, nd;  // 1/a and -b, -c, -d
+  float Lx[3];
+  float2 Ly[3], Lz[3];
 };
-__device__ __forceinline__ Coef coef_at(const Geo &g, int I, int J, int K) {
-  const float alx = __ldg(g.alpha[0] + I), aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
-  const float bex = __ldg(g.beta[0] + I), bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
-  Coef c;
-  c.ca = alx * aly * alz;
-  c.cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
-  c.cc = alx * bey * bez + bex * aly * bez + bex * bey * alz;
-  c.cd = bex * bey * bez;
-  c.Le[0] = aly * alz; c.Le[1] = alx * alz; c.Le[2] = alx * aly;
-  c.Lp[0] = aly * bez + bey * alz; c.Lp[1] = alx * bez + bex * alz; c.Lp[2] = alx * bey + bex * aly;
-  c.Lw[0] = bey * bez; c.Lw[1] = bex * bez; c.Lw[2] = bex * bey;
+__device__ __forceinline__ Coef2 coef_pair(const Geo &g, int I0, int J, int K) {
+  const float2 alx = ld2(g.alpha[0] + I0), bex = ld2(g.beta[0] + I0), iax = ld2(g.ialpha[0] + I0);
+  const float aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
+  const float bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
+  const float eyz = aly * alz, pyz = aly * bez + bey * alz, wyz = bey * bez;
+  Coef2 c;
+  c.ia = pmul(iax, bc(__ldg(g.ialpha[1] + J) * __ldg(g.ialpha[2] + K)));
+  // a = ax ay az, b = ax (ay bz + by az) + bx ay az, c = ax by bz + bx (ay bz + by az), d = bx by bz
+  c.nb = pfma(alx, bc(-pyz), pmul(bex, bc(-eyz)));
+  c.nc = pfma(alx, bc(-wyz), pmul(bex, bc(-pyz)));
+  c.nd = pmul(bex, bc(-wyz));
+  c.Lx[0] = wyz; c.Lx[1] = pyz; c.Lx[2] = eyz;
+  c.Ly[0] = pmul(bex, bc(bez)); c.Ly[1] = pfma(alx, bc(bez), pmul(bex, bc(alz))); c.Ly[2] = pmul(alx, bc(alz));
+  c.Lz[0] = pmul(bex, bc(bey)); c.Lz[1] = pfma(alx, bc(bey), pmul(bex, bc(aly))); c.Lz[2] = pmul(alx, bc(aly));
   return c;
 }
-__device__ __forceinline__ float lam_of(const Coef &c, int lv, int j) { return lv == 0 ? c.Lw[j] : (lv == 1 ? c.Lp[j] : c.Le[j]); }
 
-__device__ __forceinline__ float2 stage2(const StageArgs &a, int idx, float y0, float y1, float r0, float r1) {
-  if (a.stage == 0) return make_float2(r0, r1);
+// stage output of a node pair; MODE 0: the rate, 1: stages 1-3, 2: stage 4 (StageArgs)
+template <int MODE>
+__device__ __forceinline__ float2 stage2(const StageArgs &a, int idx, float2 y, float2 r) {
+  if (MODE == 0 || a.stage == 0) return r;
   const float2 x = ldcs2(a.X + idx);
-  if (a.stage < 4) return make_float2(x.x + a.cdt * r0, x.y + a.cdt * r1);
+  if (MODE == 1 || a.stage < 4) return pfma(bc(a.cdt), r, x);
   const float2 b = ldcs2(a.Y2 + idx), c = ldcs2(a.Y3 + idx);
-  return make_float2((-x.x + b.x + 2.f * c.x + y0) * (1.f / 3.f) + a.cdt * r0,
-                     (-x.y + b.y + 2.f * c.y + y1) * (1.f / 3.f) + a.cdt * r1);
+  return pfma(bc(1.f / 3.f), padd(pfma(bc(2.f), c, psub(b, x)), y), pmul(bc(a.cdt), r));
 }
 
-// adjoint: column j of sum_lv Lambda^lv_jj tau(T^lv) at node (I, J, K) for the node
-// whose Lambda_jj is Lj[] (levels 0..2), T read at offset o
+// adjoint: column j of sum_lv Lambda^lv_jj tau(T^lv) at node (I, J, K), the node whose
+// Lambda_jj is Lj (levels 0..2), T read at offset o (x line: one node at a time)
 template <int JAX>
 __device__ __forceinline__ float3 tau_col(const Geo &g, const float *__restrict__ Y, int S, int o, int I, int J, int K,
                                           const float Lj[3]) {
@@ -305,100 +340,111 @@ __device__ __forceinline__ float3 tau_col(const Geo &g, const float *__restrict_
   return make_float3(qj, qk, ql);
 }
 
-// adjoint: y- and z-line contributions sum_j D_j Q_cj for one node, as weighted
-// sums over the line points (C: q[+1] - q[-1]; LR: 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]))
-template <int KY, int KZ>
-__device__ __forceinline__ void adj_yz(const Geo &g, const float *__restrict__ Yn, int S, int sy, int sz, int I, int J,
-                                       int K, const Coef &cf, float f[3]) {
-  const float Ly[3] = {cf.Lw[1], cf.Lp[1], cf.Le[1]};
-#pragma unroll 1
-  for (int d = -2; d <= 2; d++) {
-    if (d == 0 || (KY == kSC && (d == -2 || d == 2))) continue;
-    const float w = KY == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f)));
-    const float3 q = tau_col<1>(g, Yn, S, d * sy, I, J + d, K, Ly);  // (yy, zy, xy) column
-    f[1] += w * q.x; f[2] += w * q.y; f[0] += w * q.z;
-  }
-  const float Lz[3] = {cf.Lw[2], cf.Lp[2], cf.Le[2]};
-#pragma unroll 1
-  for (int d = -2; d <= 2; d++) {
-    if (d == 0 || (KZ == kSC && (d == -2 || d == 2))) continue;
-    const float w = KZ == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f)));
-    const float3 q = tau_col<2>(g, Yn, S, d * sz, I, J, K + d, Lz);  // (zz, xz, yz) column
-    f[2] += w * q.x; f[0] += w * q.y; f[1] += w * q.z;
+// the same for both nodes of a pair (y and z lines), T read at offset o from the pair
+template <int JAX>
+__device__ __forceinline__ void tau_col2(const Geo &g, const float *__restrict__ Y, int S, int o, int I0, int J, int K,
+                                         const float2 Lj[3], float2 q[3]) {
+  constexpr int KAX = (JAX + 1) % 3, LAX = (JAX + 2) % 3;
+  const int me = mat_at(g, I0, J, K), mo = mat_at(g, I0 + 1, J, K);
+  const float2 lq = make_float2(__ldg(g.lam + me), __ldg(g.lam + mo));
+  const float2 muq = make_float2(__ldg(g.mu + me), __ldg(g.mu + mo));
+  const float2 mu2 = padd(muq, muq);
+  q[0] = q[1] = q[2] = bc(0.f);
+#pragma unroll
+  for (int lv = 0; lv < 3; lv++) {
+    const float *b = Y + (9 * lv + 3) * S + o;
+    const float2 tjj = ld2(b + JAX * S), tkk = ld2(b + KAX * S), tll = ld2(b + LAX * S);
+    const float2 vj = pfma(mu2, tjj, pmul(lq, padd(padd(tjj, tkk), tll)));
+    q[0] = pfma(Lj[lv], vj, q[0]);
+    q[1] = pfma(Lj[lv], pmul(muq, ld2(b + sym(KAX, JAX) * S)), q[1]);
+    q[2] = pfma(Lj[lv], pmul(muq, ld2(b + sym(LAX, JAX) * S)), q[2]);
   }
 }
 
-template <bool ADJ, int KY, int KZ>
+// adjoint: y- and z-line contributions sum_j D_j Q_cj of a pair, as weighted sums over
+// the line points (C: q[+1] - q[-1]; LR: 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]))
+template <int KY, int KZ>
+__device__ __forceinline__ void adj_yz(const Geo &g, const float *__restrict__ Yn, int S, int sy, int sz, int I0, int J,
+                                       int K, const Coef2 &cf, float2 f[3]) {
+#pragma unroll 1
+  for (int d = -2; d <= 2; d++) {
+    if (d == 0 || (KY == kSC && (d == -2 || d == 2))) continue;
+    const float2 w = bc(KY == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f))));
+    float2 q[3];
+    tau_col2<1>(g, Yn, S, d * sy, I0, J + d, K, cf.Ly, q);  // (yy, zy, xy) column
+    f[1] = pfma(w, q[0], f[1]); f[2] = pfma(w, q[1], f[2]); f[0] = pfma(w, q[2], f[0]);
+  }
+#pragma unroll 1
+  for (int d = -2; d <= 2; d++) {
+    if (d == 0 || (KZ == kSC && (d == -2 || d == 2))) continue;
+    const float2 w = bc(KZ == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f))));
+    float2 q[3];
+    tau_col2<2>(g, Yn, S, d * sz, I0, J, K + d, cf.Lz, q);  // (zz, xz, yz) column
+    f[2] = pfma(w, q[0], f[2]); f[0] = pfma(w, q[1], f[0]); f[1] = pfma(w, q[2], f[1]);
+  }
+}
+
+template <bool ADJ, int MODE, int KY, int KZ>
 __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K, bool even_ok) {
   const int S = (int)g.stride;
   const int node = (K * g.n[1] + J) * g.px + I0;
   const int sy = g.px, sz = g.px * g.n[1];
   const float *__restrict__ Yn = a.Y + node;
-  const Coef ce = coef_at(g, I0, J, K), co = coef_at(g, I0 + 1, J, K);
-  float fe[3] = {0.f, 0.f, 0.f}, fo[3] = {0.f, 0.f, 0.f};  // u-row sums (times h)
+  const Coef2 cf = coef_pair(g, I0, J, K);
+  float2 f[3] = {bc(0.f), bc(0.f), bc(0.f)};  // u-row sums (times h)
   if constexpr (ADJ) {
     // Q = sum_lv Lambda^lv_jj tau(T^lv): pointwise with the material of each line point
-    {  // x: points I0-2 .. I0+2 (Lambda_xx is the same for both nodes)
-      // even (LR) weights 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]); odd (C, at I0+1): q[+2] - q[0]
-      const float Lx[3] = {ce.Lw[0], ce.Lp[0], ce.Le[0]};
+    // x: points I0-2 .. I0+2; even (LR) weights 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]),
+    // odd (C, at I0+1): q[+2] - q[0]
 #pragma unroll 1
-      for (int d = 0; d < 5; d++) {
-        const float we = d == 0 ? 0.5f : (d == 1 ? -2.f : (d == 3 ? 2.f : (d == 4 ? -0.5f : 0.f)));
-        const float wo = d == 2 ? -1.f : (d == 4 ? 1.f : 0.f);
-        const float3 q = tau_col<0>(g, Yn, S, d - 2, I0 + d - 2, J, K, Lx);
-        fe[0] += we * q.x; fe[1] += we * q.y; fe[2] += we * q.z;
-        fo[0] += wo * q.x; fo[1] += wo * q.y; fo[2] += wo * q.z;
-      }
+    for (int d = 0; d < 5; d++) {
+      const float2 w = make_float2(d == 0 ? 0.5f : (d == 1 ? -2.f : (d == 3 ? 2.f : (d == 4 ? -0.5f : 0.f))),
+                                   d == 2 ? -1.f : (d == 4 ? 1.f : 0.f));
+      const float3 q = tau_col<0>(g, Yn, S, d - 2, I0 + d - 2, J, K, cf.Lx);
+      f[0] = pfma(w, bc(q.x), f[0]); f[1] = pfma(w, bc(q.y), f[1]); f[2] = pfma(w, bc(q.z), f[2]);
     }
-    adj_yz<KY, KZ>(g, Yn, S, sy, sz, I0, J, K, ce, fe);
-    adj_yz<KY, KZ>(g, Yn + 1, S, sy, sz, I0 + 1, J, K, co, fo);
+    adj_yz<KY, KZ>(g, Yn, S, sy, sz, I0, J, K, cf, f);
   }
-  // ---- S rows: H_ij = sum_lv Lambda^lv_jj D_j u^lv_i (times h); keep the own u values
-  float He[3][3], Ho[3][3], ue[3][3], uo[3][3];  // [i][j], [lv][i]
+  // ---- S rows: H_ij = sum_lv Lambda^lv_jj D_j u^lv_i (times h)
+  float2 s[6];
+  {
+    float2 H[3][3];  // [i][j]
 #pragma unroll
-  for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 3; i++)
 #pragma unroll
-    for (int j = 0; j < 3; j++) He[i][j] = Ho[i][j] = 0.f;
+      for (int j = 0; j < 3; j++) H[i][j] = bc(0.f);
 #pragma unroll
-  for (int lv = 0; lv < 3; lv++)
+    for (int lv = 0; lv < 3; lv++)
 #pragma unroll
-    for (int i = 0; i < 3; i++) {
-      const float *p = Yn + (9 * lv + i) * S;
-      const XWin w = xwin(p);
-      const float2 dy = dline<KY>(p, sy), dz = dline<KZ>(p, sz);
-      ue[lv][i] = w.v[2];
-      uo[lv][i] = w.v[3];
-      He[i][0] += lam_of(ce, lv, 0) * dxe(w);
-      Ho[i][0] += lam_of(co, lv, 0) * dxo(w);
-      He[i][1] += lam_of(ce, lv, 1) * dy.x;
-      Ho[i][1] += lam_of(co, lv, 1) * dy.y;
-      He[i][2] += lam_of(ce, lv, 2) * dz.x;
-      Ho[i][2] += lam_of(co, lv, 2) * dz.y;
-    }
-  float se[6] = {He[0][0], He[1][1], He[2][2], He[1][2] + He[2][1], He[0][2] + He[2][0], He[0][1] + He[1][0]};
-  float so[6] = {Ho[0][0], Ho[1][1], Ho[2][2], Ho[1][2] + Ho[2][1], Ho[0][2] + Ho[2][0], Ho[0][1] + Ho[1][0]};
+      for (int i = 0; i < 3; i++) {
+        const float *p = Yn + (9 * lv + i) * S;
+        const float2 dx = dx2(xwin(p));
+        const float2 dy = dline<KY>(p, sy), dz = dline<KZ>(p, sz);
+        H[i][0] = pfma(bc(cf.Lx[lv]), dx, H[i][0]);
+        H[i][1] = pfma(cf.Ly[lv], dy, H[i][1]);
+        H[i][2] = pfma(cf.Lz[lv], dz, H[i][2]);
+      }
+    s[0] = H[0][0]; s[1] = H[1][1]; s[2] = H[2][2];
+    s[3] = padd(H[1][2], H[2][1]); s[4] = padd(H[0][2], H[2][0]); s[5] = padd(H[0][1], H[1][0]);
+  }
   if constexpr (!ADJ) {  // tau(P(H)) with the node's own material
     const int me = mat_at(g, I0, J, K), mo = mat_at(g, I0 + 1, J, K);
-    const float le = __ldg(g.lam + me), mue = __ldg(g.mu + me), lo = __ldg(g.lam + mo), muo = __ldg(g.mu + mo);
-    const float tre = se[0] + se[1] + se[2], tro = so[0] + so[1] + so[2];
+    const float2 lm = make_float2(__ldg(g.lam + me), __ldg(g.lam + mo));
+    const float2 mu = make_float2(__ldg(g.mu + me), __ldg(g.mu + mo));
+    const float2 mu2 = padd(mu, mu);
+    const float2 ltr = pmul(lm, padd(padd(s[0], s[1]), s[2]));
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      se[c] = 2.f * mue * se[c] + le * tre;
-      so[c] = 2.f * muo * so[c] + lo * tro;
-    }
+    for (int c = 0; c < 3; c++) s[c] = pfma(mu2, s[c], ltr);
 #pragma unroll
-    for (int c = 3; c < 6; c++) {
-      se[c] *= mue;
-      so[c] *= muo;
-    }
+    for (int c = 3; c < 6; c++) s[c] = pmul(mu, s[c]);
   }
 
   // ---- u rows (times h): f_c = sum_j D_j Q_cj; forward Q = sum_lv Lambda^lv_jj S^lv
-  const float inv_h = g.inv_h;
+  const float2 ih = bc(g.inv_h);
   // S components in the order xx yy zz yz xz xy; for each: (c, j) pairs it feeds
 #pragma unroll
   for (int comp = 0; comp < 6; comp++) {
-    float s0[3], s1[3];  // own values per level, even / odd
+    float2 sv[3];  // own values per level
 #pragma unroll
     for (int lv = 0; lv < 3; lv++) {
       const float *p = Yn + (9 * lv + 3 + comp) * S;
@@ -407,59 +453,43 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
       const bool on_z = comp == 2 || comp == 3 || comp == 4;  // zz, yz, xz
       if (on_x) {
         const XWin w = xwin(p);
-        s0[lv] = w.v[2];
-        s1[lv] = w.v[3];
+        sv[lv] = make_float2(w.v[2], w.v[3]);
         if constexpr (!ADJ) {
           const int c = comp == 0 ? 0 : (comp == 5 ? 1 : 2);  // xx -> c 0, xy -> c 1, xz -> c 2 (j = x)
-          fe[c] += lam_of(ce, lv, 0) * dxe(w);
-          fo[c] += lam_of(co, lv, 0) * dxo(w);
+          f[c] = pfma(bc(cf.Lx[lv]), dx2(w), f[c]);
         }
       } else {
-        const float2 v = ld2(p);
-        s0[lv] = v.x;
-        s1[lv] = v.y;
+        sv[lv] = ld2(p);
       }
       if constexpr (!ADJ) {
         if (on_y) {
-          const float2 d = dline<KY>(p, sy);
           const int c = comp == 1 ? 1 : (comp == 5 ? 0 : 2);  // yy -> 1, xy -> 0, yz -> 2 (j = y)
-          fe[c] += lam_of(ce, lv, 1) * d.x;
-          fo[c] += lam_of(co, lv, 1) * d.y;
+          f[c] = pfma(cf.Ly[lv], dline<KY>(p, sy), f[c]);
         }
         if (on_z) {
-          const float2 d = dline<KZ>(p, sz);
           const int c = comp == 2 ? 2 : (comp == 4 ? 0 : 1);  // zz -> 2, xz -> 0, yz -> 1 (j = z)
-          fe[c] += lam_of(ce, lv, 2) * d.x;
-          fo[c] += lam_of(co, lv, 2) * d.y;
+          f[c] = pfma(cf.Lz[lv], dline<KZ>(p, sz), f[c]);
         }
       }
     }
     // stress update of this component: S'' = (src - b S' - c S - d Sbar) / a
     const int i0 = (3 + comp) * S + node, i1 = (12 + comp) * S + node, i2 = (21 + comp) * S + node;
-    const float ae = (se[comp] * inv_h - ce.cb * s0[2] - ce.cc * s0[1] - ce.cd * s0[0]) / ce.ca;
-    const float ao = (so[comp] * inv_h - co.cb * s1[2] - co.cc * s1[1] - co.cd * s1[0]) / co.ca;
-    float2 v;
-    v = stage2(a, i0, s0[0], s1[0], s0[1], s1[1]);
-    st2(a.out + i0, v.x, v.y, even_ok);
-    v = stage2(a, i1, s0[1], s1[1], s0[2], s1[2]);
-    st2(a.out + i1, v.x, v.y, even_ok);
-    v = stage2(a, i2, s0[2], s1[2], ae, ao);
-    st2(a.out + i2, v.x, v.y, even_ok);
+    const float2 acc = pmul(pfma(cf.nb, sv[2], pfma(cf.nc, sv[1], pfma(cf.nd, sv[0], pmul(s[comp], ih)))), cf.ia);
+    st2(a.out + i0, stage2<MODE>(a, i0, sv[0], sv[1]), even_ok);
+    st2(a.out + i1, stage2<MODE>(a, i1, sv[1], sv[2]), even_ok);
+    st2(a.out + i2, stage2<MODE>(a, i2, sv[2], acc), even_ok);
   }
   // ---- displacement update: u'' = (f / h) / (rho a) - (b u' + c u + d ubar) / a
-  const float sfe = inv_h / (g.rho * ce.ca), sfo = inv_h / (g.rho * co.ca);
+  // (own u values read again here rather than held since the S rows)
+  const float2 irh = bc(g.inv_rho_h);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     const int i0 = c * S + node, i1 = (9 + c) * S + node, i2 = (18 + c) * S + node;
-    const float ae = sfe * fe[c] - (ce.cb * ue[2][c] + ce.cc * ue[1][c] + ce.cd * ue[0][c]) / ce.ca;
-    const float ao = sfo * fo[c] - (co.cb * uo[2][c] + co.cc * uo[1][c] + co.cd * uo[0][c]) / co.ca;
-    float2 v;
-    v = stage2(a, i0, ue[0][c], uo[0][c], ue[1][c], uo[1][c]);
-    st2(a.out + i0, v.x, v.y, even_ok);
-    v = stage2(a, i1, ue[1][c], uo[1][c], ue[2][c], uo[2][c]);
-    st2(a.out + i1, v.x, v.y, even_ok);
-    v = stage2(a, i2, ue[2][c], uo[2][c], ae, ao);
-    st2(a.out + i2, v.x, v.y, even_ok);
+    const float2 u0 = ld2(Yn + c * S), u1 = ld2(Yn + (9 + c) * S), u2 = ld2(Yn + (18 + c) * S);
+    const float2 acc = pmul(pfma(cf.nb, u2, pfma(cf.nc, u1, pfma(cf.nd, u0, pmul(irh, f[c])))), cf.ia);
+    st2(a.out + i0, stage2<MODE>(a, i0, u0, u1), even_ok);
+    st2(a.out + i1, stage2<MODE>(a, i1, u1, u2), even_ok);
+    st2(a.out + i2, stage2<MODE>(a, i2, u2, acc), even_ok);
   }
 }
 
@@ -476,7 +506,7 @@ constexpr int kBX = 32, kBY = FWI_PML_BY;
 
 // grid.x: blocks of kBY warp tasks (see Region); tasks of a box run plane by plane.
 // The boxes exclude the outer faces of the grid, so every node takes the bulk path.
-template <bool ADJ>
+template <bool ADJ, int MODE>
 __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, StageArgs a, Region r) {
   const int task = blockIdx.x * kBY + threadIdx.y;
   if (task >= r.tasks_before[r.nbox]) return;
@@ -504,11 +534,11 @@ __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, Stag
     // in the box; the even node may not be (its results are dropped)
     const bool even_ok = I0 >= r.lo[b][0];
     if (ky == kSC) {
-      if (kz == kSC) pml_pair<ADJ, kSC, kSC>(g, a, I0, J, K, even_ok);
-      else pml_pair<ADJ, kSC, kSLR>(g, a, I0, J, K, even_ok);
+      if (kz == kSC) pml_pair<ADJ, MODE, kSC, kSC>(g, a, I0, J, K, even_ok);
+      else pml_pair<ADJ, MODE, kSC, kSLR>(g, a, I0, J, K, even_ok);
     } else {
-      if (kz == kSC) pml_pair<ADJ, kSLR, kSC>(g, a, I0, J, K, even_ok);
-      else pml_pair<ADJ, kSLR, kSLR>(g, a, I0, J, K, even_ok);
+      if (kz == kSC) pml_pair<ADJ, MODE, kSLR, kSC>(g, a, I0, J, K, even_ok);
+      else pml_pair<ADJ, MODE, kSLR, kSLR>(g, a, I0, J, K, even_ok);
     }
   }
 }
@@ -570,10 +600,16 @@ void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) 
   const int tasks = r.tasks_before[r.nbox];
   if (tasks == 0) return;
   const dim3 grd((tasks + kBY - 1) / kBY), blk(kBX, kBY);
-  if (adjoint)
-    pml_kernel<true><<<grd, blk, 0, s>>>(g, a, r);
-  else
-    pml_kernel<false><<<grd, blk, 0, s>>>(g, a, r);
+  const int mode = a.stage == 0 ? 0 : (a.stage < 4 ? 1 : 2);
+  if (adjoint) {
+    if (mode == 0) pml_kernel<true, 0><<<grd, blk, 0, s>>>(g, a, r);
+    else if (mode == 1) pml_kernel<true, 1><<<grd, blk, 0, s>>>(g, a, r);
+    else pml_kernel<true, 2><<<grd, blk, 0, s>>>(g, a, r);
+  } else {
+    if (mode == 0) pml_kernel<false, 0><<<grd, blk, 0, s>>>(g, a, r);
+    else if (mode == 1) pml_kernel<false, 1><<<grd, blk, 0, s>>>(g, a, r);
+    else pml_kernel<false, 2><<<grd, blk, 0, s>>>(g, a, r);
+  }
 }
 
 void launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
