@@ -72,144 +72,6 @@ __device__ __forceinline__ float stage_value(const StageArgs &a, int idx, float 
   return (-__ldcs(a.X + idx) + __ldcs(a.Y2 + idx) + 2.f * __ldcs(a.Y3 + idx) + yv) * (1.f / 3.f) + a.cdt * rate;
 }
 
-template <bool ADJ>
-__device__ void pml_node(const Geo &g, const StageArgs &a, int I, int J, int K) {
-  const int S = (int)g.stride;
-  const int node = (K * g.n[1] + J) * g.px + I;
-  const int st[3] = {1, g.px, g.px * g.n[1]};
-  const int kind[3] = {side_kind(I, g.n[0]), side_kind(J, g.n[1]), side_kind(K, g.n[2])};
-  const bool dir = I == 0 || I == g.n[0] - 1 || J == 0 || J == g.n[1] - 1 || K == g.n[2] - 1 ||
-                   (g.top_dir && K == 0);
-  const float *__restrict__ Y = a.Y;
-  const float alx = __ldg(g.alpha[0] + I), aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
-  const float bex = __ldg(g.beta[0] + I), bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
-  const float ca = alx * aly * alz;
-  const float cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
-  const float cc = alx * bey * bez + bex * aly * bez + bex * bey * alz;
-  const float cd = bex * bey * bez;
-  const float Le[3] = {aly * alz, alx * alz, alx * aly};
-  const float Lp[3] = {aly * bez + bey * alz, alx * bez + bex * alz, alx * bey + bex * aly};
-  const float Lw[3] = {bey * bez, bex * bez, bex * bey};
-  const float inv_a = 1.f / ca;
-  const float inv_h = g.inv_h;
-  float lam = 0.f, mu = 0.f;
-  {
-    int i = I - 2 * g.lo[0], j = J - 2 * g.lo[1], k = K - 2 * g.lo[2];
-    i = i < 0 ? 0 : (i >= g.m[0] ? g.m[0] - 1 : i);
-    j = j < 0 ? 0 : (j >= g.m[1] ? g.m[1] - 1 : j);
-    k = k < 0 ? 0 : (k >= g.m[2] ? g.m[2] - 1 : k);
-    const int mi = (k * g.m[1] + j) * g.m[0] + i;
-    if (!ADJ) {
-      lam = __ldg(g.lam + mi);
-      mu = __ldg(g.mu + mi);
-    }
-  }
-
-  // ---- displacement rows
-  if (!dir) {
-    float f[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-      const int k = (j + 1) % 3, l = (j + 2) % 3;
-      const int kd = kind[j];
-      const int s = st[j];
-      const float Lv[3] = {Lw[j], Lp[j], Le[j]};
-      // Q column j at offsets -2..2 along j (only the ones the kind uses)
-      float q[3][5];
-#pragma unroll
-      for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int d = 0; d < 5; d++) q[c][d] = 0.f;
-#pragma unroll
-      for (int d = 0; d < 5; d++) {
-        const int off = d - 2;
-        const bool used = kd == kSC ? (off == -1 || off == 1)
-                                    : (kd == kSLR ? off != 0 : off >= 0);
-        if (!used) continue;
-        const int o = node + off * s;
-        float vj = 0.f, vk = 0.f, vl = 0.f;
-        if (!ADJ) {
-#pragma unroll
-          for (int lv = 0; lv < 3; lv++) {
-            const float *b = Y + (9 * lv + 3) * S;
-            vj += Lv[lv] * __ldg(b + sym(j, j) * S + o);
-            vk += Lv[lv] * __ldg(b + sym(k, j) * S + o);
-            vl += Lv[lv] * __ldg(b + sym(l, j) * S + o);
-          }
-        } else {
-          int cq[3] = {I, J, K};
-          cq[j] += off;
-          int i2 = cq[0] - 2 * g.lo[0], j2 = cq[1] - 2 * g.lo[1], k2 = cq[2] - 2 * g.lo[2];
-          i2 = i2 < 0 ? 0 : (i2 >= g.m[0] ? g.m[0] - 1 : i2);
-          j2 = j2 < 0 ? 0 : (j2 >= g.m[1] ? g.m[1] - 1 : j2);
-          k2 = k2 < 0 ? 0 : (k2 >= g.m[2] ? g.m[2] - 1 : k2);
-          const int mq = (k2 * g.m[1] + j2) * g.m[0] + i2;
-          const float lq = __ldg(g.lam + mq), muq = __ldg(g.mu + mq);
-#pragma unroll
-          for (int lv = 0; lv < 3; lv++) {
-            const float *b = Y + (9 * lv + 3) * S;
-            const float tjj = __ldg(b + j * S + o), tkk = __ldg(b + k * S + o), tll = __ldg(b + l * S + o);
-            vj += Lv[lv] * (2.f * muq * tjj + lq * (tjj + tkk + tll));
-            vk += Lv[lv] * (muq * __ldg(b + sym(k, j) * S + o));
-            vl += Lv[lv] * (muq * __ldg(b + sym(l, j) * S + o));
-          }
-        }
-        q[0][d] = vj;
-        q[1][d] = vk;
-        q[2][d] = vl;
-      }
-      f[j] += ddiv(q[0][0], q[0][1], q[0][2], q[0][3], q[0][4], kd);
-      f[k] += ddiv(q[1][0], q[1][1], q[1][2], q[1][3], q[1][4], kd);
-      f[l] += ddiv(q[2][0], q[2][1], q[2][2], q[2][3], q[2][4], kd);
-    }
-    const float sf = inv_h / (g.rho * ca);
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      const int i0 = c * S + node, i1 = (9 + c) * S + node, i2 = (18 + c) * S + node;
-      const float u0 = __ldg(Y + i0), u1 = __ldg(Y + i1), u2 = __ldg(Y + i2);
-      const float acc = sf * f[c] - (cb * u2 + cc * u1 + cd * u0) * inv_a;
-      __stcs(a.out + (i0), stage_value(a, i0, u0, u1));
-      __stcs(a.out + (i1), stage_value(a, i1, u1, u2));
-      __stcs(a.out + (i2), stage_value(a, i2, u2, acc));
-    }
-  } else if (a.stage == 0) {
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      __stcs(a.out + (c * S + node), 0.f);
-      __stcs(a.out + ((9 + c) * S + node), 0.f);
-      __stcs(a.out + ((18 + c) * S + node), 0.f);
-    }
-  }
-
-  // ---- stress rows
-  float H[3][3];
-#pragma unroll
-  for (int j = 0; j < 3; j++) {
-    const int s = st[j], kd = kind[j];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-      H[i][j] = inv_h * (Le[j] * dav(Y + (18 + i) * S, node, s, kd) + Lp[j] * dav(Y + (9 + i) * S, node, s, kd) +
-                         Lw[j] * dav(Y + i * S, node, s, kd));
-  }
-  float src[6] = {H[0][0], H[1][1], H[2][2], H[1][2] + H[2][1], H[0][2] + H[2][0], H[0][1] + H[1][0]};
-  if (!ADJ) {
-    const float tr = src[0] + src[1] + src[2];
-#pragma unroll
-    for (int c = 0; c < 3; c++) src[c] = 2.f * mu * src[c] + lam * tr;
-#pragma unroll
-    for (int c = 3; c < 6; c++) src[c] = mu * src[c];
-  }
-#pragma unroll
-  for (int c = 0; c < 6; c++) {
-    const int i0 = (3 + c) * S + node, i1 = (12 + c) * S + node, i2 = (21 + c) * S + node;
-    const float s0 = __ldg(Y + i0), s1 = __ldg(Y + i1), s2 = __ldg(Y + i2);
-    __stcs(a.out + (i0), stage_value(a, i0, s0, s1));
-    __stcs(a.out + (i1), stage_value(a, i1, s1, s2));
-    __stcs(a.out + (i2), stage_value(a, i2, s2, (src[c] - cb * s2 - cc * s1 - cd * s0) * inv_a));
-  }
-}
-
-
 __device__ __forceinline__ int mat_at(const Geo &g, int I, int J, int K) {
   int i = I - 2 * g.lo[0], j = J - 2 * g.lo[1], k = K - 2 * g.lo[2];
   i = i < 0 ? 0 : (i >= g.m[0] ? g.m[0] - 1 : i);
@@ -493,6 +355,152 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
   }
 }
 
+// ---------------------------------------------------------------------------
+// PML nodes on the outer faces of the grid (fixed faces, and the free top face
+// outside the interior), from a list built once per context, with the general
+// side kinds (one-sided on the faces). A block owns 32 list nodes and has three
+// warps: warp j first forms the axis-j terms (the u-row divergence along j and
+// column j of H) into shared memory, then warp w writes displacement component w
+// and stress components w and w + 3.
+constexpr int kFaceNodes = 32;
+
+struct FaceCtx {
+  int node, st[3], kind[3];
+  bool dir;
+  float cb, cc, cd, inv_a, Le[3], Lp[3], Lw[3];
+};
+
+struct FaceShared {
+  float f[3][3][kFaceNodes];  // [axis][component][node]: u-row divergence terms (times h)
+  float H[3][3][kFaceNodes];  // [i][j][node] (times 1)
+};
+
+__device__ __forceinline__ FaceCtx face_ctx(const Geo &g, int I, int J, int K) {
+  FaceCtx n;
+  n.node = (K * g.n[1] + J) * g.px + I;
+  n.st[0] = 1; n.st[1] = g.px; n.st[2] = g.px * g.n[1];
+  n.kind[0] = side_kind(I, g.n[0]); n.kind[1] = side_kind(J, g.n[1]); n.kind[2] = side_kind(K, g.n[2]);
+  n.dir = I == 0 || I == g.n[0] - 1 || J == 0 || J == g.n[1] - 1 || K == g.n[2] - 1 || (g.top_dir && K == 0);
+  const float alx = __ldg(g.alpha[0] + I), aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
+  const float bex = __ldg(g.beta[0] + I), bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
+  n.cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
+  n.cc = alx * bey * bez + bex * aly * bez + bex * bey * alz;
+  n.cd = bex * bey * bez;
+  n.Le[0] = aly * alz; n.Le[1] = alx * alz; n.Le[2] = alx * aly;
+  n.Lp[0] = aly * bez + bey * alz; n.Lp[1] = alx * bez + bex * alz; n.Lp[2] = alx * bey + bex * aly;
+  n.Lw[0] = bey * bez; n.Lw[1] = bex * bez; n.Lw[2] = bex * bey;
+  n.inv_a = __ldg(g.ialpha[0] + I) * __ldg(g.ialpha[1] + J) * __ldg(g.ialpha[2] + K);
+  return n;
+}
+
+template <bool ADJ, int JA>
+__device__ __forceinline__ void face_axis(const Geo &g, const StageArgs &a, const FaceCtx &n, int I, int J, int K,
+                                          FaceShared &sh, int lane) {
+  constexpr int KA = (JA + 1) % 3, LA = (JA + 2) % 3;
+  const int S = (int)g.stride;
+  const float *__restrict__ Y = a.Y;
+  const int kd = n.kind[JA], s = n.st[JA];
+  if (!n.dir) {
+    // Q column JA at offsets -2..2 along JA (only the ones the kind uses)
+    const float Lv[3] = {n.Lw[JA], n.Lp[JA], n.Le[JA]};
+    float q[3][5];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int d = 0; d < 5; d++) q[c][d] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 5; d++) {
+      const int off = d - 2;
+      const bool used = kd == kSC ? (off == -1 || off == 1) : (kd == kSLR ? off != 0 : off >= 0);
+      if (!used) continue;
+      const int o = n.node + off * s;
+      float vj = 0.f, vk = 0.f, vl = 0.f;
+      if (!ADJ) {
+#pragma unroll
+        for (int lv = 0; lv < 3; lv++) {
+          const float *b = Y + (9 * lv + 3) * S;
+          vj += Lv[lv] * __ldg(b + sym(JA, JA) * S + o);
+          vk += Lv[lv] * __ldg(b + sym(KA, JA) * S + o);
+          vl += Lv[lv] * __ldg(b + sym(LA, JA) * S + o);
+        }
+      } else {
+        int cq[3] = {I, J, K};
+        cq[JA] += off;
+        const int mq = mat_at(g, cq[0], cq[1], cq[2]);
+        const float lq = __ldg(g.lam + mq), muq = __ldg(g.mu + mq);
+#pragma unroll
+        for (int lv = 0; lv < 3; lv++) {
+          const float *b = Y + (9 * lv + 3) * S;
+          const float tjj = __ldg(b + JA * S + o), tkk = __ldg(b + KA * S + o), tll = __ldg(b + LA * S + o);
+          vj += Lv[lv] * (2.f * muq * tjj + lq * (tjj + tkk + tll));
+          vk += Lv[lv] * (muq * __ldg(b + sym(KA, JA) * S + o));
+          vl += Lv[lv] * (muq * __ldg(b + sym(LA, JA) * S + o));
+        }
+      }
+      q[0][d] = vj;
+      q[1][d] = vk;
+      q[2][d] = vl;
+    }
+    sh.f[JA][JA][lane] = ddiv(q[0][0], q[0][1], q[0][2], q[0][3], q[0][4], kd);
+    sh.f[JA][KA][lane] = ddiv(q[1][0], q[1][1], q[1][2], q[1][3], q[1][4], kd);
+    sh.f[JA][LA][lane] = ddiv(q[2][0], q[2][1], q[2][2], q[2][3], q[2][4], kd);
+  }
+  // column JA of H (times h)
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+    sh.H[i][JA][lane] = n.Le[JA] * dav(Y + (18 + i) * S, n.node, s, kd) + n.Lp[JA] * dav(Y + (9 + i) * S, n.node, s, kd) +
+                        n.Lw[JA] * dav(Y + i * S, n.node, s, kd);
+}
+
+template <bool ADJ>
+__device__ __forceinline__ void face_write(const Geo &g, const StageArgs &a, const FaceCtx &n, int I, int J, int K,
+                                           const FaceShared &sh, int lane, int w) {
+  const int S = (int)g.stride;
+  const float *__restrict__ Y = a.Y;
+  // ---- displacement component w
+  {
+    const int c = w;
+    const int i0 = c * S + n.node, i1 = (9 + c) * S + n.node, i2 = (18 + c) * S + n.node;
+    if (!n.dir) {
+      const float f = sh.f[0][c][lane] + sh.f[1][c][lane] + sh.f[2][c][lane];
+      const float u0 = __ldg(Y + i0), u1 = __ldg(Y + i1), u2 = __ldg(Y + i2);
+      const float acc = (g.inv_rho_h * f - (n.cb * u2 + n.cc * u1 + n.cd * u0)) * n.inv_a;
+      __stcs(a.out + i0, stage_value(a, i0, u0, u1));
+      __stcs(a.out + i1, stage_value(a, i1, u1, u2));
+      __stcs(a.out + i2, stage_value(a, i2, u2, acc));
+    } else if (a.stage == 0) {
+      __stcs(a.out + i0, 0.f);
+      __stcs(a.out + i1, 0.f);
+      __stcs(a.out + i2, 0.f);
+    }
+  }
+  // ---- stress components w and w + 3: S'' = (tau(P(H)) / h - b S' - c S - d Sbar) / a
+  float lam = 0.f, mu = 0.f;
+  if (!ADJ) {
+    const int mi = mat_at(g, I, J, K);
+    lam = __ldg(g.lam + mi);
+    mu = __ldg(g.mu + mi);
+  }
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int c = w + 3 * h;
+    float src;
+    if (h == 0) {
+      src = sh.H[w][w][lane];
+      if (!ADJ) src = 2.f * mu * src + lam * (sh.H[0][0][lane] + sh.H[1][1][lane] + sh.H[2][2][lane]);
+    } else {
+      const int i = w == 2 ? 0 : (w == 1 ? 0 : 1), j = w == 2 ? 1 : 2;  // yz, xz, xy
+      src = sh.H[i][j][lane] + sh.H[j][i][lane];
+      if (!ADJ) src = mu * src;
+    }
+    const int i0 = (3 + c) * S + n.node, i1 = (12 + c) * S + n.node, i2 = (21 + c) * S + n.node;
+    const float s0 = __ldg(Y + i0), s1 = __ldg(Y + i1), s2 = __ldg(Y + i2);
+    __stcs(a.out + i0, stage_value(a, i0, s0, s1));
+    __stcs(a.out + i1, stage_value(a, i1, s1, s2));
+    __stcs(a.out + i2, stage_value(a, i2, s2, (g.inv_h * src - n.cb * s2 - n.cc * s1 - n.cd * s0) * n.inv_a));
+  }
+}
+
 #ifndef FWI_PML_BY
 #define FWI_PML_BY 4
 #endif
@@ -500,7 +508,7 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
 #define FWI_PML_MINB 6
 #endif
 #ifndef FWI_FACE_MINB
-#define FWI_FACE_MINB 1
+#define FWI_FACE_MINB 8
 #endif
 constexpr int kBX = 32, kBY = FWI_PML_BY;
 
@@ -543,15 +551,27 @@ __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, Stag
   }
 }
 
-// PML nodes on the outer faces of the grid (fixed faces, and the free top face
-// outside the interior), from a list built once per context: generic path
 template <bool ADJ>
-__global__ void __launch_bounds__(128, FWI_FACE_MINB) pml_face_kernel(Geo g, StageArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.nface) return;
-  const int node = g.face[i];
-  const int I = node % g.px, rr = node / g.px;
-  pml_node<ADJ>(g, a, I, rr % g.n[1], rr / g.n[1]);
+__global__ void __launch_bounds__(3 * kFaceNodes, FWI_FACE_MINB) pml_face_kernel(Geo g, StageArgs a) {
+  __shared__ FaceShared sh;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int i = blockIdx.x * kFaceNodes + lane;
+  const bool live = i < g.nface;
+  int I = 0, J = 0, K = 0;
+  FaceCtx n;
+  if (live) {
+    const int node = g.face[i];
+    const int rr = node / g.px;
+    I = node % g.px;
+    J = rr % g.n[1];
+    K = rr / g.n[1];
+    n = face_ctx(g, I, J, K);
+    if (w == 0) face_axis<ADJ, 0>(g, a, n, I, J, K, sh, lane);
+    else if (w == 1) face_axis<ADJ, 1>(g, a, n, I, J, K, sh, lane);
+    else face_axis<ADJ, 2>(g, a, n, I, J, K, sh, lane);
+  }
+  __syncthreads();
+  if (live) face_write<ADJ>(g, a, n, I, J, K, sh, lane, w);
 }
 
 }  // namespace
@@ -614,11 +634,12 @@ void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) 
 
 void launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
   if (g.nface <= 0) return;
-  const int nb = (g.nface + 127) / 128;
+  const int nb = (g.nface + kFaceNodes - 1) / kFaceNodes;
+  const dim3 blk(kFaceNodes, 3);
   if (adjoint)
-    pml_face_kernel<true><<<nb, 128, 0, s>>>(g, a);
+    pml_face_kernel<true><<<nb, blk, 0, s>>>(g, a);
   else
-    pml_face_kernel<false><<<nb, 128, 0, s>>>(g, a);
+    pml_face_kernel<false><<<nb, blk, 0, s>>>(g, a);
 }
 
 }  // namespace fwi

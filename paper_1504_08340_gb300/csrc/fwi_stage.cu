@@ -282,130 +282,176 @@ __device__ __forceinline__ void pml_strain_axis(const Geo &g, const float *__res
   H[2][j] = h2;
 }
 
-template <bool ADJ>
-__device__ __forceinline__ void general_node(const Geo &g, const StageArgs &a, int I, int J, int K) {
-  const int64_t node = ((int64_t)K * g.n[1] + J) * g.px + I;
-  const int c3[3] = {I, J, K};
-  const int64_t st[3] = {1, (int64_t)g.px, (int64_t)g.px * g.n[1]};
-  const Ax ax[3] = {make_ax(I, g.n[0], g.lo[0], g.hi[0]), make_ax(J, g.n[1], g.lo[1], g.hi[1]),
-                    make_ax(K, g.n[2], g.lo[2], g.hi[2])};
-  const int64_t S = g.stride;
-  const float *__restrict__ Y = a.Y;
-  const bool dir = I == 0 || I == g.n[0] - 1 || J == 0 || J == g.n[1] - 1 || K == g.n[2] - 1 ||
-                   (g.top_dir && K == 0);
-  const int nel = ax[0].ns * ax[1].ns * ax[2].ns;
-  const int npml = nel - nrd(ax[0]) * nrd(ax[1]) * nrd(ax[2]);
-  const bool pml = npml > 0;
+// per-node quantities shared by both phases of shell_kernel
+struct NodeCtx {
+  int64_t node;
+  int c3[3];
+  int64_t st[3];
+  Ax ax[3];
+  bool dir, pml;
+  int nel, npml;
+  float cb, cc, cd, inv_a, Le[3], Lp[3], Lw[3];
+};
 
+__device__ __forceinline__ NodeCtx node_ctx(const Geo &g, int I, int J, int K) {
+  NodeCtx n;
+  n.node = ((int64_t)K * g.n[1] + J) * g.px + I;
+  n.c3[0] = I; n.c3[1] = J; n.c3[2] = K;
+  n.st[0] = 1; n.st[1] = g.px; n.st[2] = (int64_t)g.px * g.n[1];
+  n.ax[0] = make_ax(I, g.n[0], g.lo[0], g.hi[0]);
+  n.ax[1] = make_ax(J, g.n[1], g.lo[1], g.hi[1]);
+  n.ax[2] = make_ax(K, g.n[2], g.lo[2], g.hi[2]);
+  n.dir = I == 0 || I == g.n[0] - 1 || J == 0 || J == g.n[1] - 1 || K == g.n[2] - 1 || (g.top_dir && K == 0);
+  n.nel = n.ax[0].ns * n.ax[1].ns * n.ax[2].ns;
+  n.npml = n.nel - nrd(n.ax[0]) * nrd(n.ax[1]) * nrd(n.ax[2]);
+  n.pml = n.npml > 0;
   // stretch coefficients at the node (products of eps_x eps_y eps_z)
   const float alx = __ldg(g.alpha[0] + I), aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
   const float bex = __ldg(g.beta[0] + I), bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
-  const float ca = alx * aly * alz;
-  const float cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
-  const float cc = alx * bey * bez + bex * aly * bez + bex * bey * alz;
-  const float cd = bex * bey * bez;
-  const float Le[3] = {aly * alz, alx * alz, alx * aly};
-  const float Lp[3] = {aly * bez + bey * alz, alx * bez + bex * alz, alx * bey + bex * aly};
-  const float Lw[3] = {bey * bez, bex * bez, bex * bey};
-  const float inv_a = 1.f / ca;
-
-  // ---- displacement rows
-  if (!dir) {
-    float fr[3] = {0.f, 0.f, 0.f}, fp[3] = {0.f, 0.f, 0.f};
-    const float *__restrict__ U = Y + 9 * S;
-    interior_force_axis<0>(g, U, node, c3, st, ax, false, fr);
-    interior_force_axis<1>(g, U, node, c3, st, ax, false, fr);
-    interior_force_axis<2>(g, U, node, c3, st, ax, false, fr);
-    if (pml) {
-      pml_force_axis<ADJ, 0>(g, Y, node, c3, st, ax, Le, Lp, Lw, fp);
-      pml_force_axis<ADJ, 1>(g, Y, node, c3, st, ax, Le, Lp, Lw, fp);
-      pml_force_axis<ADJ, 2>(g, Y, node, c3, st, ax, Le, Lp, Lw, fp);
-    }
-    const float s_rd = g.inv_h * g.inv_h * (1.f / 3.f), s_pml = g.inv_h * (1.f / 3.f);
-    const float inv_m = 1.f / (g.rho * ca * (float)nel);
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      const int64_t i0 = (int64_t)c * S + node, i1 = (int64_t)(9 + c) * S + node, i2 = (int64_t)(18 + c) * S + node;
-      const float u0 = __ldg(Y + i0), u1 = __ldg(Y + i1), u2 = __ldg(Y + i2);
-      const float acc = -(s_rd * fr[c] + s_pml * fp[c]) * inv_m - (cb * u2 + cc * u1 + cd * u0) * inv_a;
-      if (pml || a.stage == 0) __stcs(a.out + (i0), stage_value(a, i0, pml ? u1 : 0.f));
-      const float v1 = stage_value(a, i1, u2);
-      __stcs(a.out + (i1), v1);
-      __stcs(a.out + (i2), stage_value(a, i2, acc));
-      if (a.hist) write_hist(g, a, I, J, K, c, v1);
-    }
-  } else if (a.stage == 0) {
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      __stcs(a.out + ((int64_t)c * S + node), 0.f);
-      __stcs(a.out + ((int64_t)(9 + c) * S + node), 0.f);
-      __stcs(a.out + ((int64_t)(18 + c) * S + node), 0.f);
-    }
-  }
-
-  // ---- stress rows (PML nodes)
-  if (pml) {
-    float H[3][3];
-    pml_strain_axis<0>(g, Y, node, st, ax, Le, Lp, Lw, H);
-    pml_strain_axis<1>(g, Y, node, st, ax, Le, Lp, Lw, H);
-    pml_strain_axis<2>(g, Y, node, st, ax, Le, Lp, Lw, H);
-    const float sc = g.inv_h / (float)npml;
-    // P(H): diagonal H_ii, off-diagonal H_ij + H_ji; order xx yy zz yz xz xy
-    float src[6] = {sc * H[0][0], sc * H[1][1], sc * H[2][2], sc * (H[1][2] + H[2][1]), sc * (H[0][2] + H[2][0]),
-                    sc * (H[0][1] + H[1][0])};
-    if (!ADJ) {  // tau(P(H)) = mu (P + diag P) + lambda tr(P) I
-      const int64_t mi = mat_index(g, I, J, K);
-      const float lam = __ldg(g.lam + mi), mu = __ldg(g.mu + mi);
-      const float tr = src[0] + src[1] + src[2];
-#pragma unroll
-      for (int c = 0; c < 3; c++) src[c] = 2.f * mu * src[c] + lam * tr;
-#pragma unroll
-      for (int c = 3; c < 6; c++) src[c] = mu * src[c];
-    }
-#pragma unroll
-    for (int c = 0; c < 6; c++) {
-      const int64_t i0 = (int64_t)(3 + c) * S + node, i1 = (int64_t)(12 + c) * S + node,
-                    i2 = (int64_t)(21 + c) * S + node;
-      const float s0 = __ldg(Y + i0), s1 = __ldg(Y + i1), s2 = __ldg(Y + i2);
-      __stcs(a.out + (i0), stage_value(a, i0, s1));
-      __stcs(a.out + (i1), stage_value(a, i1, s2));
-      __stcs(a.out + (i2), stage_value(a, i2, (src[c] - cb * s2 - cc * s1 - cd * s0) * inv_a));
-    }
-  } else if (a.stage == 0) {
-#pragma unroll
-    for (int c = 0; c < 6; c++) {
-      __stcs(a.out + ((int64_t)(3 + c) * S + node), 0.f);
-      __stcs(a.out + ((int64_t)(12 + c) * S + node), 0.f);
-      __stcs(a.out + ((int64_t)(21 + c) * S + node), 0.f);
-    }
-  }
+  n.cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
+  n.cc = alx * bey * bez + bex * aly * bez + bex * bey * alz;
+  n.cd = bex * bey * bez;
+  n.Le[0] = aly * alz; n.Le[1] = alx * alz; n.Le[2] = alx * aly;
+  n.Lp[0] = aly * bez + bey * alz; n.Lp[1] = alx * bez + bex * alz; n.Lp[2] = alx * bey + bex * aly;
+  n.Lw[0] = bey * bez; n.Lw[1] = bex * bez; n.Lw[2] = bex * bey;
+  n.inv_a = __ldg(g.ialpha[0] + I) * __ldg(g.ialpha[1] + J) * __ldg(g.ialpha[2] + K);
+  return n;
 }
 
 // Interface shell: nodes of the closed interior box [2lo, 2hi] (free top: from
 // k = 0) outside the open box of interior_kernel, i.e. the nodes shared by
 // interior and PML elements (and, without a PML, the fixed outer faces). Their
 // node numbers come from a list built once per context (g.shell, g.nshell).
+//
+// A block owns 32 list nodes and has three warps. In the first phase warp j forms
+// the axis-j terms of every sum at its nodes (the element line quadratures along j
+// of the u rows, column j of H of the S rows) and leaves them in shared memory; in
+// the second phase warp w writes displacement component w and stress components
+// w and w + 3 of the same nodes.
+constexpr int kShellNodes = 32;
+
+struct ShellShared {
+  float f[3][3][kShellNodes];  // [axis][component][node]: u-row terms s_rd fr + s_pml fp of one axis
+  float H[3][3][kShellNodes];  // [i][j][node]
+};
+
+template <bool ADJ, int J>
+__device__ __forceinline__ void shell_axis(const Geo &g, const StageArgs &a, const NodeCtx &n, ShellShared &sh,
+                                           int lane) {
+  const float *__restrict__ Y = a.Y;
+  const int64_t S = g.stride;
+  if (!n.dir) {
+    float fr[3] = {0.f, 0.f, 0.f}, fp[3] = {0.f, 0.f, 0.f};
+    interior_force_axis<J>(g, Y + 9 * S, n.node, n.c3, n.st, n.ax, false, fr);
+    if (n.pml) pml_force_axis<ADJ, J>(g, Y, n.node, n.c3, n.st, n.ax, n.Le, n.Lp, n.Lw, fp);
+    const float s_rd = g.inv_h * g.inv_h * (1.f / 3.f), s_pml = g.inv_h * (1.f / 3.f);
+#pragma unroll
+    for (int c = 0; c < 3; c++) sh.f[J][c][lane] = s_rd * fr[c] + s_pml * fp[c];
+  }
+  if (n.pml) {
+    float H[3][3];
+    pml_strain_axis<J>(g, Y, n.node, n.st, n.ax, n.Le, n.Lp, n.Lw, H);
+#pragma unroll
+    for (int i = 0; i < 3; i++) sh.H[i][J][lane] = H[i][J];
+  }
+}
+
+// stress component c (order xx yy zz yz xz xy) of the node: its three levels
 template <bool ADJ>
+__device__ __forceinline__ void shell_stress(const Geo &g, const StageArgs &a, const NodeCtx &n,
+                                             const ShellShared &sh, int lane, int c) {
+  const int64_t S = g.stride;
+  const float *__restrict__ Y = a.Y;
+  const int64_t i0 = (int64_t)(3 + c) * S + n.node, i1 = (int64_t)(12 + c) * S + n.node,
+                i2 = (int64_t)(21 + c) * S + n.node;
+  if (!n.pml) {
+    if (a.stage == 0) {
+      __stcs(a.out + i0, 0.f);
+      __stcs(a.out + i1, 0.f);
+      __stcs(a.out + i2, 0.f);
+    }
+    return;
+  }
+  const float sc = g.inv_h / (float)n.npml;
+  // P(H): diagonal H_ii, off-diagonal H_ij + H_ji
+  auto P = [&](int k) {
+    if (k < 3) return sc * sh.H[k][k][lane];
+    const int i = k == 5 ? 0 : (k == 4 ? 0 : 1), j = k == 5 ? 1 : 2;  // xy, xz, yz
+    return sc * (sh.H[i][j][lane] + sh.H[j][i][lane]);
+  };
+  float src = P(c);
+  if (!ADJ) {  // tau(P(H)) = mu (P + diag P) + lambda tr(P) I
+    const int64_t mi = mat_index(g, n.c3[0], n.c3[1], n.c3[2]);
+    const float lam = __ldg(g.lam + mi), mu = __ldg(g.mu + mi);
+    src = c < 3 ? 2.f * mu * src + lam * (P(0) + P(1) + P(2)) : mu * src;
+  }
+  const float s0 = __ldg(Y + i0), s1 = __ldg(Y + i1), s2 = __ldg(Y + i2);
+  __stcs(a.out + i0, stage_value(a, i0, s1));
+  __stcs(a.out + i1, stage_value(a, i1, s2));
+  __stcs(a.out + i2, stage_value(a, i2, (src - n.cb * s2 - n.cc * s1 - n.cd * s0) * n.inv_a));
+}
+
+// displacement component c of the node: its three levels
+__device__ __forceinline__ void shell_disp(const Geo &g, const StageArgs &a, const NodeCtx &n, const ShellShared &sh,
+                                           int lane, int c) {
+  const int64_t S = g.stride;
+  const float *__restrict__ Y = a.Y;
+  const int64_t i0 = (int64_t)c * S + n.node, i1 = (int64_t)(9 + c) * S + n.node, i2 = (int64_t)(18 + c) * S + n.node;
+  if (n.dir) {
+    if (a.stage == 0) {
+      __stcs(a.out + i0, 0.f);
+      __stcs(a.out + i1, 0.f);
+      __stcs(a.out + i2, 0.f);
+    }
+    return;
+  }
+  const float fsum = sh.f[0][c][lane] + sh.f[1][c][lane] + sh.f[2][c][lane];
+  const float inv_m = n.inv_a / (g.rho * (float)n.nel);
+  const float u0 = __ldg(Y + i0), u1 = __ldg(Y + i1), u2 = __ldg(Y + i2);
+  const float acc = -fsum * inv_m - (n.cb * u2 + n.cc * u1 + n.cd * u0) * n.inv_a;
+  if (n.pml || a.stage == 0) __stcs(a.out + i0, stage_value(a, i0, n.pml ? u1 : 0.f));
+  const float v1 = stage_value(a, i1, u2);
+  __stcs(a.out + i1, v1);
+  __stcs(a.out + i2, stage_value(a, i2, acc));
+  if (a.hist) write_hist(g, a, n.c3[0], n.c3[1], n.c3[2], c, v1);
+}
+
 #ifndef FWI_SHELL_MINB
-#define FWI_SHELL_MINB 4
+#define FWI_SHELL_MINB 5
 #endif
-__global__ void __launch_bounds__(128, FWI_SHELL_MINB) shell_kernel(Geo g, StageArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.nshell) return;
-  const int node = g.shell[i];
-  const int I = node % g.px, r = node / g.px;
-  general_node<ADJ>(g, a, I, r % g.n[1], r / g.n[1]);
+template <bool ADJ>
+__global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(Geo g, StageArgs a) {
+  __shared__ ShellShared sh;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int i = blockIdx.x * kShellNodes + lane;
+  const bool live = i < g.nshell;
+  NodeCtx n;
+  if (live) {
+    const int node = g.shell[i];
+    const int I = node % g.px, r = node / g.px;
+    n = node_ctx(g, I, r % g.n[1], r / g.n[1]);
+    if (w == 0) shell_axis<ADJ, 0>(g, a, n, sh, lane);
+    else if (w == 1) shell_axis<ADJ, 1>(g, a, n, sh, lane);
+    else shell_axis<ADJ, 2>(g, a, n, sh, lane);
+  }
+  __syncthreads();
+  if (live) {
+    shell_disp(g, a, n, sh, lane, w);
+    shell_stress<ADJ>(g, a, n, sh, lane, w);
+    shell_stress<ADJ>(g, a, n, sh, lane, w + 3);
+  }
 }
 
 }  // namespace
 
 void launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
   if (g.nshell > 0) {
-    const int nb = (g.nshell + 127) / 128;
+    const int nb = (g.nshell + kShellNodes - 1) / kShellNodes;
+    const dim3 blk(kShellNodes, 3);
     if (adjoint)
-      shell_kernel<true><<<nb, 128, 0, s>>>(g, a);
+      shell_kernel<true><<<nb, blk, 0, s>>>(g, a);
     else
-      shell_kernel<false><<<nb, 128, 0, s>>>(g, a);
+      shell_kernel<false><<<nb, blk, 0, s>>>(g, a);
   }
   launch_pml_face(g, a, adjoint, s);
 }
