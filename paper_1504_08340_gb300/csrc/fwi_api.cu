@@ -530,19 +530,8 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
           const bool in_closed = i >= c0[0] && i <= c1[0] && j >= c0[1] && j <= c1[1] && k >= c0[2] && k <= c1[2];
           if (!in_closed) face.push_back((k * g.n[1] + j) * g.px + i);
         }
-    // group the list entries by coordinate parity (and by face position inside a group)
-    // so that the 32 nodes of a warp take the same side-type branches
-    auto by_parity = [&](std::vector<int> &v) {
-      std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
-        auto key = [&](int n) {
-          const int i = n % g.px, r = n / g.px, j = r % g.n[1], k = r / g.n[1];
-          return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-        };
-        return key(a) < key(b);
-      });
-    };
-    by_parity(shell);
-    by_parity(face);
+    // both lists stay in (k, j, i) order: the nodes of a warp are neighbours in memory,
+    // and their stencil rows are shared
     g.nface = (int)face.size();
     if (g.nface > 0) {
       st = dalloc(c, &c->d_face, face.size());

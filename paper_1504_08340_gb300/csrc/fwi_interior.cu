@@ -186,7 +186,7 @@ __device__ __forceinline__ void load_own(const Geo &g, const StageArgs &a, int64
   for (int c = 0; c < 3; c++) {
     const int64_t i1 = (int64_t)(9 + c) * S + node, i2 = (int64_t)(18 + c) * S + node;
     o.yd[c] = __ldg(a.Y + i2);
-    if (a.stage >= 1) {
+    if (a.stage >= 2) {  // in stage 1 X is the stage input
       o.x1[c] = __ldcs(a.X + i1);
       o.x2[c] = __ldcs(a.X + i2);
     }
@@ -196,6 +196,7 @@ __device__ __forceinline__ void load_own(const Geo &g, const StageArgs &a, int64
 // RK4 stage update (see StageArgs); stage 4 reads Y2 and Y3 here
 __device__ __forceinline__ float stage_value(const StageArgs &a, int64_t idx, float x, float yv, float rate) {
   if (a.stage == 0) return rate;
+  if (a.stage == 1) return yv + a.cdt * rate;
   if (a.stage < 4) return x + a.cdt * rate;
   return (-x + __ldcs(a.Y2 + idx) + 2.f * __ldcs(a.Y3 + idx) + yv) * (1.f / 3.f) + a.cdt * rate;
 }

@@ -36,7 +36,7 @@ struct Geo {
 
 // One RK4 stage over every node (see fwi_kernels.cu).
 //  stage 0: out = rate(Y)                   (fwi_rhs)
-//  stage 1..3: out = X + cdt * rate(Y)
+//  stage 1..3: out = X + cdt * rate(Y)   (stage 1: X must be Y; the kernels read Y only)
 //  stage 4: out = (-X + Y2 + 2 Y3 + Y)/3 + cdt * rate(Y)   (out may alias X)
 struct StageArgs {
   const float *Y;    // stage input

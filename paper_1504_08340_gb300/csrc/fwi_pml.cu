@@ -54,20 +54,25 @@ __device__ __forceinline__ float ddiv(float g_m2, float g_m1, float g0, float g_
 
 __host__ __device__ constexpr int sym(int i, int j) { return i == j ? i : (i + j == 1 ? 5 : (i + j == 2 ? 4 : 3)); }
 
-// PML boxes and their warp tasks. A warp task is R rows of one plane with equal
-// y parity (J0, J0 + 2, ..., J0 + 2(R-1)), R = 32 / (node pairs per row) for narrow
-// boxes, else R = 1 (the warp walks the row in chunks of 32 pairs). The side kinds
-// along y and z are then uniform across the warp.
+// PML boxes and their warp tasks. The node pairs of a box row are cut into nseg
+// x segments of at most `per` <= 32 pairs. A warp task is one segment of R rows of
+// one plane with equal y parity (J0, J0 + 2, ..., J0 + 2(R-1)): R = 32 / per for
+// narrow boxes, else 1. The side kinds along y and z are then uniform across the
+// warp. Tasks run segment by segment, so the warps resident at one time cover one
+// x segment of many rows and planes, and the rows that their y and z stencils
+// share stay in L2.
 struct Region {
   int nbox;
   int lo[6][3], hi[6][3];  // inclusive node boxes
   int P[6], R[6];          // node pairs per row, rows per warp task
+  int nseg[6], per[6];     // x segments per row, pairs per segment (the last may have fewer)
   int jfirst[6][2], nj[6][2], groups[6][2];  // per y-parity class: first J, row count, warp groups per plane
   int tasks_before[7];     // prefix sums of warp tasks per box
 };
 
 __device__ __forceinline__ float stage_value(const StageArgs &a, int idx, float yv, float rate) {
   if (a.stage == 0) return rate;
+  if (a.stage == 1) return yv + a.cdt * rate;  // X is the stage input
   if (a.stage < 4) return __ldcs(a.X + idx) + a.cdt * rate;
   return (-__ldcs(a.X + idx) + __ldcs(a.Y2 + idx) + 2.f * __ldcs(a.Y3 + idx) + yv) * (1.f / 3.f) + a.cdt * rate;
 }
@@ -172,12 +177,14 @@ __device__ __forceinline__ Coef2 coef_pair(const Geo &g, int I0, int J, int K) {
   return c;
 }
 
-// stage output of a node pair; MODE 0: the rate, 1: stages 1-3, 2: stage 4 (StageArgs)
+// stage output of a node pair from its own input value y and rate r; MODE 0: the
+// rate, 1: stage 1 (X is the stage input, so x = y), 2: stages 2-3, 3: stage 4
 template <int MODE>
 __device__ __forceinline__ float2 stage2(const StageArgs &a, int idx, float2 y, float2 r) {
-  if (MODE == 0 || a.stage == 0) return r;
+  if constexpr (MODE == 0) return r;
+  if constexpr (MODE == 1) return pfma(bc(a.cdt), r, y);
   const float2 x = ldcs2(a.X + idx);
-  if (MODE == 1 || a.stage < 4) return pfma(bc(a.cdt), r, x);
+  if constexpr (MODE == 2) return pfma(bc(a.cdt), r, x);
   const float2 b = ldcs2(a.Y2 + idx), c = ldcs2(a.Y3 + idx);
   return pfma(bc(1.f / 3.f), padd(pfma(bc(2.f), c, psub(b, x)), y), pmul(bc(a.cdt), r));
 }
@@ -505,7 +512,7 @@ __device__ __forceinline__ void face_write(const Geo &g, const StageArgs &a, con
 #define FWI_PML_BY 4
 #endif
 #ifndef FWI_PML_MINB
-#define FWI_PML_MINB 6
+#define FWI_PML_MINB 7
 #endif
 #ifndef FWI_FACE_MINB
 #define FWI_FACE_MINB 8
@@ -520,13 +527,15 @@ __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, Stag
   if (task >= r.tasks_before[r.nbox]) return;
   int b = 0;
   while (b + 1 < r.nbox && task >= r.tasks_before[b + 1]) b++;
-  const int t = task - r.tasks_before[b];
   const int G = r.groups[b][0] + r.groups[b][1];
+  const int per_seg = G * (r.hi[b][2] - r.lo[b][2] + 1);  // tasks of one x segment
+  const int t = (task - r.tasks_before[b]) % per_seg;
+  const int pb = (task - r.tasks_before[b]) / per_seg * r.per[b];  // first pair of the segment
   const int K = r.lo[b][2] + t / G;
   int q = t % G;
   const int cls = q < r.groups[b][0] ? 0 : 1;
   if (cls) q -= r.groups[b][0];
-  const int P = r.P[b], R = r.R[b];
+  const int P = min(r.per[b], r.P[b] - pb), R = r.R[b];  // pairs of this segment
   const int x0 = r.lo[b][0] & ~1;  // pairs start at even x
   const int kz = side_kind(K, g.n[2]);
   const int ky = side_kind(r.jfirst[b][cls], g.n[1]);
@@ -534,12 +543,11 @@ __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, Stag
   const int jrow = q * R + rr;
   if (rr >= R || jrow >= r.nj[b][cls]) return;
   const int J = r.jfirst[b][cls] + 2 * jrow;
-  const int p0 = R > 1 ? threadIdx.x % P : threadIdx.x;
-  const int pstep = R > 1 ? P : kBX;
-  for (int p = p0; p < P; p += pstep) {
-    const int I0 = x0 + 2 * p;
-    // box x-ranges start and end at odd nodes, so the odd node of a pair is always
-    // in the box; the even node may not be (its results are dropped)
+  const int p = R > 1 ? threadIdx.x % P : threadIdx.x;  // pair of the segment (P <= 32)
+  if (p < P) {
+    const int I0 = x0 + 2 * (pb + p);
+    // box x-ranges end at odd nodes, so the odd node of a pair is always in the box;
+    // the even node of a box's first pair may not be (its results are dropped)
     const bool even_ok = I0 >= r.lo[b][0];
     if (ky == kSC) {
       if (kz == kSC) pml_pair<ADJ, MODE, kSC, kSC>(g, a, I0, J, K, even_ok);
@@ -600,7 +608,9 @@ static Region pml_region(const Geo &g) {
   r.tasks_before[0] = 0;
   for (int b = 0; b < r.nbox; b++) {
     r.P[b] = (r.hi[b][0] - (r.lo[b][0] & ~1)) / 2 + 1;
-    r.R[b] = r.P[b] >= 16 ? 1 : 32 / r.P[b];
+    r.nseg[b] = (r.P[b] + 31) / 32;
+    r.per[b] = (r.P[b] + r.nseg[b] - 1) / r.nseg[b];
+    r.R[b] = r.per[b] >= 16 ? 1 : 32 / r.per[b];
     int per_plane = 0;
     for (int c = 0; c < 2; c++) {
       const int jf = r.lo[b][1] + ((r.lo[b][1] & 1) != c ? 1 : 0);  // first J of parity c
@@ -609,7 +619,7 @@ static Region pml_region(const Geo &g) {
       r.groups[b][c] = (r.nj[b][c] + r.R[b] - 1) / r.R[b];
       per_plane += r.groups[b][c];
     }
-    r.tasks_before[b + 1] = r.tasks_before[b] + per_plane * (r.hi[b][2] - r.lo[b][2] + 1);
+    r.tasks_before[b + 1] = r.tasks_before[b] + r.nseg[b] * per_plane * (r.hi[b][2] - r.lo[b][2] + 1);
   }
   for (int b = r.nbox; b < 6; b++) r.tasks_before[b + 1] = r.tasks_before[b];
   return r;
@@ -620,15 +630,17 @@ void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) 
   const int tasks = r.tasks_before[r.nbox];
   if (tasks == 0) return;
   const dim3 grd((tasks + kBY - 1) / kBY), blk(kBX, kBY);
-  const int mode = a.stage == 0 ? 0 : (a.stage < 4 ? 1 : 2);
+  const int mode = a.stage == 0 ? 0 : (a.stage == 1 ? 1 : (a.stage < 4 ? 2 : 3));
   if (adjoint) {
     if (mode == 0) pml_kernel<true, 0><<<grd, blk, 0, s>>>(g, a, r);
     else if (mode == 1) pml_kernel<true, 1><<<grd, blk, 0, s>>>(g, a, r);
-    else pml_kernel<true, 2><<<grd, blk, 0, s>>>(g, a, r);
+    else if (mode == 2) pml_kernel<true, 2><<<grd, blk, 0, s>>>(g, a, r);
+    else pml_kernel<true, 3><<<grd, blk, 0, s>>>(g, a, r);
   } else {
     if (mode == 0) pml_kernel<false, 0><<<grd, blk, 0, s>>>(g, a, r);
     else if (mode == 1) pml_kernel<false, 1><<<grd, blk, 0, s>>>(g, a, r);
-    else pml_kernel<false, 2><<<grd, blk, 0, s>>>(g, a, r);
+    else if (mode == 2) pml_kernel<false, 2><<<grd, blk, 0, s>>>(g, a, r);
+    else pml_kernel<false, 3><<<grd, blk, 0, s>>>(g, a, r);
   }
 }
 

@@ -111,12 +111,13 @@ __device__ __forceinline__ int64_t mat_index(const Geo &g, int I, int J, int K) 
   return ((int64_t)k * g.m[1] + j) * g.m[0] + i;
 }
 
-// RK4 stage update of one field value (see StageArgs)
-__device__ __forceinline__ float stage_value(const StageArgs &a, int64_t idx, float rate) {
+// RK4 stage update of one field value with stage-input value yv (see StageArgs;
+// in stage 1 X is the stage input)
+__device__ __forceinline__ float stage_value(const StageArgs &a, int64_t idx, float yv, float rate) {
   if (a.stage == 0) return rate;
+  if (a.stage == 1) return yv + a.cdt * rate;
   if (a.stage < 4) return __ldcs(a.X + idx) + a.cdt * rate;
-  return (-__ldcs(a.X + idx) + __ldcs(a.Y2 + idx) + 2.f * __ldcs(a.Y3 + idx) + __ldg(a.Y + idx)) * (1.f / 3.f) +
-         a.cdt * rate;
+  return (-__ldcs(a.X + idx) + __ldcs(a.Y2 + idx) + 2.f * __ldcs(a.Y3 + idx) + yv) * (1.f / 3.f) + a.cdt * rate;
 }
 
 __device__ __forceinline__ void write_hist(const Geo &g, const StageArgs &a, int I, int J, int K, int c, float v) {
@@ -386,9 +387,9 @@ __device__ __forceinline__ void shell_stress(const Geo &g, const StageArgs &a, c
     src = c < 3 ? 2.f * mu * src + lam * (P(0) + P(1) + P(2)) : mu * src;
   }
   const float s0 = __ldg(Y + i0), s1 = __ldg(Y + i1), s2 = __ldg(Y + i2);
-  __stcs(a.out + i0, stage_value(a, i0, s1));
-  __stcs(a.out + i1, stage_value(a, i1, s2));
-  __stcs(a.out + i2, stage_value(a, i2, (src - n.cb * s2 - n.cc * s1 - n.cd * s0) * n.inv_a));
+  __stcs(a.out + i0, stage_value(a, i0, s0, s1));
+  __stcs(a.out + i1, stage_value(a, i1, s1, s2));
+  __stcs(a.out + i2, stage_value(a, i2, s2, (src - n.cb * s2 - n.cc * s1 - n.cd * s0) * n.inv_a));
 }
 
 // displacement component c of the node: its three levels
@@ -409,10 +410,10 @@ __device__ __forceinline__ void shell_disp(const Geo &g, const StageArgs &a, con
   const float inv_m = n.inv_a / (g.rho * (float)n.nel);
   const float u0 = __ldg(Y + i0), u1 = __ldg(Y + i1), u2 = __ldg(Y + i2);
   const float acc = -fsum * inv_m - (n.cb * u2 + n.cc * u1 + n.cd * u0) * n.inv_a;
-  if (n.pml || a.stage == 0) __stcs(a.out + i0, stage_value(a, i0, n.pml ? u1 : 0.f));
-  const float v1 = stage_value(a, i1, u2);
+  if (n.pml || a.stage == 0) __stcs(a.out + i0, stage_value(a, i0, u0, n.pml ? u1 : 0.f));
+  const float v1 = stage_value(a, i1, u1, u2);
   __stcs(a.out + i1, v1);
-  __stcs(a.out + i2, stage_value(a, i2, acc));
+  __stcs(a.out + i2, stage_value(a, i2, u2, acc));
   if (a.hist) write_hist(g, a, n.c3[0], n.c3[1], n.c3[2], c, v1);
 }
 
