@@ -374,6 +374,7 @@ constexpr int kFaceNodes = 32;
 struct FaceCtx {
   int node, st[3], kind[3];
   bool dir;
+  bool flat[3];  // the line along this axis through the node lies in a fixed face
   float cb, cc, cd, inv_a, Le[3], Lp[3], Lw[3];
 };
 
@@ -387,7 +388,12 @@ __device__ __forceinline__ FaceCtx face_ctx(const Geo &g, int I, int J, int K) {
   n.node = (K * g.n[1] + J) * g.px + I;
   n.st[0] = 1; n.st[1] = g.px; n.st[2] = g.px * g.n[1];
   n.kind[0] = side_kind(I, g.n[0]); n.kind[1] = side_kind(J, g.n[1]); n.kind[2] = side_kind(K, g.n[2]);
-  n.dir = I == 0 || I == g.n[0] - 1 || J == 0 || J == g.n[1] - 1 || K == g.n[2] - 1 || (g.top_dir && K == 0);
+  const bool fx = I == 0 || I == g.n[0] - 1, fy = J == 0 || J == g.n[1] - 1,
+             fz = K == g.n[2] - 1 || (g.top_dir && K == 0);
+  n.dir = fx || fy || fz;
+  n.flat[0] = fy || fz;
+  n.flat[1] = fx || fz;
+  n.flat[2] = fx || fy;
   const float alx = __ldg(g.alpha[0] + I), aly = __ldg(g.alpha[1] + J), alz = __ldg(g.alpha[2] + K);
   const float bex = __ldg(g.beta[0] + I), bey = __ldg(g.beta[1] + J), bez = __ldg(g.beta[2] + K);
   n.cb = alx * aly * bez + alx * bey * alz + bex * aly * alz;
@@ -452,7 +458,13 @@ __device__ __forceinline__ void face_axis(const Geo &g, const StageArgs &a, cons
     sh.f[JA][KA][lane] = ddiv(q[1][0], q[1][1], q[1][2], q[1][3], q[1][4], kd);
     sh.f[JA][LA][lane] = ddiv(q[2][0], q[2][1], q[2][2], q[2][3], q[2][4], kd);
   }
-  // column JA of H (times h)
+  // column JA of H (times h). Every displacement level is zero on a fixed face, so
+  // the derivative along a line that lies in one is exactly zero.
+  if (n.flat[JA]) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) sh.H[i][JA][lane] = 0.f;
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 3; i++)
     sh.H[i][JA][lane] = n.Le[JA] * dav(Y + (18 + i) * S, n.node, s, kd) + n.Lp[JA] * dav(Y + (9 + i) * S, n.node, s, kd) +
