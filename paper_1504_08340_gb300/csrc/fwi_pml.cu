@@ -544,17 +544,17 @@ __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, Stag
   const int t = (task - r.tasks_before[b]) % per_seg;
   const int pb = (task - r.tasks_before[b]) / per_seg * r.per[b];  // first pair of the segment
   const int K = r.lo[b][2] + t / G;
-  int q = t % G;
-  const int cls = q < r.groups[b][0] ? 0 : 1;
-  if (cls) q -= r.groups[b][0];
+  const int qa = t % G;
   const int P = min(r.per[b], r.P[b] - pb), R = r.R[b];  // pairs of this segment
   const int x0 = r.lo[b][0] & ~1;  // pairs start at even x
   const int kz = side_kind(K, g.n[2]);
-  const int ky = side_kind(r.jfirst[b][cls], g.n[1]);
-  const int rr = R > 1 ? threadIdx.x / P : 0;   // row of the group handled by this lane
+  const int cls = qa < r.groups[b][0] ? 0 : 1;
+  const int q = cls ? qa - r.groups[b][0] : qa;
+  const int rr = R > 1 ? threadIdx.x / P : 0;  // row of the group handled by this lane
   const int jrow = q * R + rr;
   if (rr >= R || jrow >= r.nj[b][cls]) return;
   const int J = r.jfirst[b][cls] + 2 * jrow;
+  const int ky = side_kind(r.jfirst[b][cls], g.n[1]);
   const int p = R > 1 ? threadIdx.x % P : threadIdx.x;  // pair of the segment (P <= 32)
   if (p < P) {
     const int I0 = x0 + 2 * (pb + p);

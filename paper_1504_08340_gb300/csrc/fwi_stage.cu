@@ -162,7 +162,7 @@ __device__ __forceinline__ void interior_force_axis(const Geo &g, const float *_
   constexpr int k = (j + 1) % 3, l = (j + 2) % 3;
   const float invw = (c3[j] & 1) ? 0.75f : 3.0f;
   float acc_j = 0.f, acc_k = 0.f, acc_l = 0.f;
-#pragma unroll
+#pragma unroll 1
   for (int sj = 0; sj < 2; sj++) {
     if (sj >= ax[j].ns) continue;
     const int t = sj == 0 ? ax[j].t0 : ax[j].t1;
@@ -171,7 +171,7 @@ __device__ __forceinline__ void interior_force_axis(const Geo &g, const float *_
     const float nk = all_sides ? (float)ax[k].ns : (float)nrd(ax[k]);
     const float nl = all_sides ? (float)ax[l].ns : (float)nrd(ax[l]);
     if (nk == 0.f || nl == 0.f) continue;
-#pragma unroll
+#pragma unroll 1
     for (int p = 0; p < 3; p++) {
       const float cf = line_coef(t, p);
       if (cf == 0.f) continue;
@@ -203,7 +203,7 @@ __device__ __forceinline__ void pml_force_axis(const Geo &g, const float *__rest
   const float invw = (c3[j] & 1) ? 0.75f : 3.0f;
   const float Lv[3] = {Lw[j], Lp[j], Le[j]};  // history, value, rate levels
   float acc_j = 0.f, acc_k = 0.f, acc_l = 0.f;
-#pragma unroll
+#pragma unroll 1
   for (int sj = 0; sj < 2; sj++) {
     if (sj >= ax[j].ns) continue;
     const int t = sj == 0 ? ax[j].t0 : ax[j].t1;
@@ -211,7 +211,7 @@ __device__ __forceinline__ void pml_force_axis(const Geo &g, const float *__rest
     const int cpml = ax[k].ns * ax[l].ns - (rdj ? nrd(ax[k]) * nrd(ax[l]) : 0);
     if (cpml == 0) continue;
     float qj = 0.f, qk = 0.f, ql = 0.f;
-#pragma unroll
+#pragma unroll 1
     for (int p = 0; p < 3; p++) {
       const float cf = line_coef(t, p);
       if (cf == 0.f) continue;
@@ -263,7 +263,7 @@ __device__ __forceinline__ void pml_strain_axis(const Geo &g, const float *__res
   constexpr int k = (j + 1) % 3, l = (j + 2) % 3;
   const int64_t S = g.stride;
   float h0 = 0.f, h1 = 0.f, h2 = 0.f;
-#pragma unroll
+#pragma unroll 1
   for (int sj = 0; sj < 2; sj++) {
     if (sj >= ax[j].ns) continue;
     const int t = sj == 0 ? ax[j].t0 : ax[j].t1;
@@ -418,7 +418,7 @@ __device__ __forceinline__ void shell_disp(const Geo &g, const StageArgs &a, con
 }
 
 #ifndef FWI_SHELL_MINB
-#define FWI_SHELL_MINB 6
+#define FWI_SHELL_MINB 7
 #endif
 template <bool ADJ>
 __global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(Geo g, StageArgs a) {
