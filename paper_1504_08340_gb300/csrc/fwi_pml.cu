@@ -189,27 +189,8 @@ __device__ __forceinline__ float2 stage2(const StageArgs &a, int idx, float2 y, 
   return pfma(bc(1.f / 3.f), padd(pfma(bc(2.f), c, psub(b, x)), y), pmul(bc(a.cdt), r));
 }
 
-// adjoint: column j of sum_lv Lambda^lv_jj tau(T^lv) at node (I, J, K), the node whose
-// Lambda_jj is Lj (levels 0..2), T read at offset o (x line: one node at a time)
-template <int JAX>
-__device__ __forceinline__ float3 tau_col(const Geo &g, const float *__restrict__ Y, int S, int o, int I, int J, int K,
-                                          const float Lj[3]) {
-  constexpr int KAX = (JAX + 1) % 3, LAX = (JAX + 2) % 3;
-  const int mq = mat_at(g, I, J, K);
-  const float lq = __ldg(g.lam + mq), muq = __ldg(g.mu + mq);
-  float qj = 0.f, qk = 0.f, ql = 0.f;
-#pragma unroll
-  for (int lv = 0; lv < 3; lv++) {
-    const float *b = Y + (9 * lv + 3) * S + o;
-    const float tjj = __ldg(b + JAX * S), tkk = __ldg(b + KAX * S), tll = __ldg(b + LAX * S);
-    qj += Lj[lv] * (2.f * muq * tjj + lq * (tjj + tkk + tll));
-    qk += Lj[lv] * (muq * __ldg(b + sym(KAX, JAX) * S));
-    ql += Lj[lv] * (muq * __ldg(b + sym(LAX, JAX) * S));
-  }
-  return make_float3(qj, qk, ql);
-}
-
-// the same for both nodes of a pair (y and z lines), T read at offset o from the pair
+// adjoint: column j of sum_lv Lambda^lv_jj tau(T^lv) at the nodes (I0, J, K) and
+// (I0 + 1, J, K), whose Lambda_jj are Lj (levels 0..2), T read at offset o from the pair
 template <int JAX>
 __device__ __forceinline__ void tau_col2(const Geo &g, const float *__restrict__ Y, int S, int o, int I0, int J, int K,
                                          const float2 Lj[3], float2 q[3]) {
@@ -262,15 +243,22 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
   const Coef2 cf = coef_pair(g, I0, J, K);
   float2 f[3] = {bc(0.f), bc(0.f), bc(0.f)};  // u-row sums (times h)
   if constexpr (ADJ) {
-    // Q = sum_lv Lambda^lv_jj tau(T^lv): pointwise with the material of each line point
-    // x: points I0-2 .. I0+2; even (LR) weights 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]),
-    // odd (C, at I0+1): q[+2] - q[0]
-#pragma unroll 1
-    for (int d = 0; d < 5; d++) {
-      const float2 w = make_float2(d == 0 ? 0.5f : (d == 1 ? -2.f : (d == 3 ? 2.f : (d == 4 ? -0.5f : 0.f))),
-                                   d == 2 ? -1.f : (d == 4 ? 1.f : 0.f));
-      const float3 q = tau_col<0>(g, Yn, S, d - 2, I0 + d - 2, J, K, cf.Lx);
-      f[0] = pfma(w, bc(q.x), f[0]); f[1] = pfma(w, bc(q.y), f[1]); f[2] = pfma(w, bc(q.z), f[2]);
+    // Q = sum_lv Lambda^lv_jj tau(T^lv): pointwise with the material of each line point.
+    // x: Q at the points I0-2 .. I0+3 as three aligned pairs (the last point is not
+    // used); even node (LR): 0.5 Q[-2] - 2 Q[-1] + 2 Q[+1] - 0.5 Q[+2], odd node (C,
+    // at I0+1): Q[+2] - Q[0]
+    {
+      const float2 Lx[3] = {bc(cf.Lx[0]), bc(cf.Lx[1]), bc(cf.Lx[2])};
+      float2 qm[3], q0[3], qp[3];  // pairs (I0-2, I0-1), (I0, I0+1), (I0+2, I0+3)
+      tau_col2<0>(g, Yn, S, -2, I0 - 2, J, K, Lx, qm);
+      tau_col2<0>(g, Yn, S, 0, I0, J, K, Lx, q0);
+      tau_col2<0>(g, Yn, S, 2, I0 + 2, J, K, Lx, qp);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {  // q[0], q[1], q[2]: the xx, yx, zx entries -> components x, y, z
+        const float e = 0.5f * (qm[c].x - qp[c].x) + 2.f * (q0[c].y - qm[c].y);
+        const float o = qp[c].x - q0[c].x;
+        f[c] = padd(f[c], make_float2(e, o));
+      }
     }
     adj_yz<KY, KZ>(g, Yn, S, sy, sz, I0, J, K, cf, f);
   }

@@ -418,7 +418,7 @@ __device__ __forceinline__ void shell_disp(const Geo &g, const StageArgs &a, con
 }
 
 #ifndef FWI_SHELL_MINB
-#define FWI_SHELL_MINB 7
+#define FWI_SHELL_MINB 8
 #endif
 template <bool ADJ>
 __global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(Geo g, StageArgs a) {
