@@ -27,7 +27,13 @@ namespace fwi {
 namespace {
 
 constexpr int kTP = 32;             // node pairs per tile row (64 nodes)
-constexpr int kTY = 8;              // rows per tile
+#ifndef FWI_INT_TY
+#define FWI_INT_TY 8
+#endif
+#ifndef FWI_INT_KC
+#define FWI_INT_KC 8
+#endif
+constexpr int kTY = FWI_INT_TY;     // rows per tile
 constexpr int kTXS = 2 * kTP + 4;   // smem row pitch (halo 2 on each side)
 constexpr int kTYS = kTY + 4;
 constexpr int kFS = kTXS * kTYS;    // floats per field and plane
@@ -38,7 +44,7 @@ constexpr int kNF = FWI_INT_MAT_SMEM ? 5 : 3;  // u_x, u_y, u_z (, lambda, mu)
 constexpr int kPS = kNF * kFS;      // floats per plane
 constexpr int kRing = 6;            // planes K-2 .. K+2 in use, K+3 in flight
 constexpr int kSmem = kRing * kPS * (int)sizeof(float);
-constexpr int kKC = 4;              // planes per block
+constexpr int kKC = FWI_INT_KC;     // planes per block
 
 enum { kC = 0, kL = 1, kR = 2 };
 // side set of a node along an axis: odd coordinate {C}, even {L, R}, top face {R}
