@@ -98,19 +98,27 @@ __global__ void __launch_bounds__(256) gradient_kernel(Geo g, const float *__res
   const int64_t sm[3] = {1, (int64_t)g.m[0], (int64_t)g.m[0] * g.m[1]};
   Axis ax[3] = {axis_info(I, g.n[0], g.lo[0], g.hi[0]), axis_info(J, g.n[1], g.lo[1], g.hi[1]),
                 axis_info(K, g.n[2], g.lo[2], g.hi[2])};
+  // all loops have fixed trip counts and are unrolled, so the arrays stay in registers
   float dw[3][2][3], du[3][2][3];  // [axis][side][component]
+#pragma unroll
   for (int x = 0; x < 3; x++)
-    for (int s = 0; s < ax[x].ns; s++) {
-      if (!ax[x].rd[s]) continue;
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      const bool used = s < ax[x].ns && ax[x].rd[s];
+#pragma unroll
       for (int c = 0; c < 3; c++) {
-        dw[x][s][c] = dstc(ws + (int64_t)(9 + c) * g.stride, node, sn[x], ax[x].type[s]) * g.inv_h;
-        du[x][s][c] = dstc(uh + (int64_t)c * g.nmat, mi, sm[x], ax[x].type[s]) * g.inv_h;
+        dw[x][s][c] = used ? dstc(ws + (int64_t)(9 + c) * g.stride, node, sn[x], ax[x].type[s]) * g.inv_h : 0.f;
+        du[x][s][c] = used ? dstc(uh + (int64_t)c * g.nmat, mi, sm[x], ax[x].type[s]) * g.inv_h : 0.f;
       }
     }
   float sl = 0.f, smu = 0.f;
-  for (int sx = 0; sx < ax[0].ns; sx++)
-    for (int sy = 0; sy < ax[1].ns; sy++)
-      for (int sz = 0; sz < ax[2].ns; sz++) {
+#pragma unroll
+  for (int sx = 0; sx < 2; sx++)
+#pragma unroll
+    for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+      for (int sz = 0; sz < 2; sz++) {
+        if (sx >= ax[0].ns || sy >= ax[1].ns || sz >= ax[2].ns) continue;
         if (!(ax[0].rd[sx] && ax[1].rd[sy] && ax[2].rd[sz])) continue;
         const int s[3] = {sx, sy, sz};
         float Gw[3][3], Gu[3][3];  // G[i][j] = d v_i / d x_j
@@ -129,6 +137,7 @@ __global__ void __launch_bounds__(256) gradient_kernel(Geo g, const float *__res
                (Gw[1][2] + Gw[2][1]) * (Gu[2][1] + Gu[1][2]);
       }
   float W = g.wdetj;
+#pragma unroll
   for (int x = 0; x < 3; x++) W *= (c3[x] & 1) ? (4.f / 3.f) : (1.f / 3.f);
   gl[mi] -= wdt * (double)W * (double)sl;
   gm[mi] -= wdt * (double)W * (double)smu;

@@ -515,7 +515,7 @@ __device__ __forceinline__ void face_write(const Geo &g, const StageArgs &a, con
 #define FWI_PML_MINB 7
 #endif
 #ifndef FWI_FACE_MINB
-#define FWI_FACE_MINB 8
+#define FWI_FACE_MINB 10
 #endif
 constexpr int kBX = 32, kBY = FWI_PML_BY;
 
