@@ -185,6 +185,22 @@ fwi_status fwi_step(fwi_ctx *ctx, const float *observed, int on_device, const fw
 /* Forget the L-BFGS pairs (e.g. when the source wavelet changes, Sec. 3.3.2). */
 fwi_status fwi_step_reset(fwi_ctx *ctx);
 
+/* How fwi_adjoint_gradient and fwi_step give the adjoint sweep the forward
+ * displacement u(t_n) that the gradient integrals (C.1f)/(C.1g) need at every step:
+ *   interval = 0 (default): the forward sweep stores u at every step
+ *     ((nsteps + 1) * 3 * dims[4] floats of device memory);
+ *   interval > 0: the forward sweep stores its full RK4 state every `interval`
+ *     steps (ceil(nsteps / interval) snapshots of 27 * dims[5] floats). The adjoint
+ *     sweep then walks the segments backwards and recomputes each segment's forward
+ *     steps from its snapshot, in a second state set, into an (interval + 1)-level
+ *     history, before running the adjoint steps of that segment;
+ *   interval < 0: interval = ceil(sqrt(nsteps)), the sqrt(T) checkpointing scheme.
+ * Checkpointing costs one more forward sweep. The recomputed steps repeat the
+ * forward arithmetic exactly, so J and the gradients are bit-identical to those of
+ * interval 0. The paper does not say how u(t) reaches the gradient. Memory is
+ * allocated by the next gradient call. Errors: FWI_E_INVAL (null context). */
+fwi_status fwi_set_checkpointing(fwi_ctx *ctx, int interval);
+
 /* Current material ([k][j][i] as in fwi_set_material; host or device). */
 fwi_status fwi_get_material(fwi_ctx *ctx, float *lambda, float *mu, int on_device);
 

@@ -57,7 +57,14 @@ struct fwi_ctx {
   int d_J_cap = 0;
   int *d_flag = nullptr;
   float *d_hist = nullptr;
+  size_t hist_cap = 0;  // history slots (levels) d_hist holds
   double *d_gl = nullptr, *d_gm = nullptr;
+
+  // forward-state checkpointing of the adjoint sweep (fwi_set_checkpointing)
+  int ckpt = 0;                 // 0: full displacement history; > 0: snapshot interval; < 0: ceil(sqrt(N))
+  float *rstate[4] = {nullptr, nullptr, nullptr, nullptr};  // RK4 state set of the forward recompute
+  float *d_snap = nullptr;      // snapshots of X, [segment][27 * stride]
+  size_t snap_cap = 0;          // snapshots d_snap holds
 
   // reduced-space update (fwi_step): model, gradient, direction, L-BFGS pairs (FP64)
   int lb_cap = 0, lb_count = 0, lb_head = 0;
@@ -310,14 +317,19 @@ fwi_status ensure_trace_buffers(fwi_ctx *c) {
   return FWI_OK;
 }
 
-// forward sweep of one shot into d_traces; hist: optional displacement history
-fwi_status forward_sweep(fwi_ctx *c, int shot, float *hist) {
+// forward sweep of one shot into d_traces; hist: optional displacement history;
+// snap: optional snapshots of the step-start state X every `every` steps
+fwi_status forward_sweep(fwi_ctx *c, int shot, float *hist, float *snap = nullptr, int every = 0) {
   TRY(zero_state(c));
   const int64_t per_step = (int64_t)c->nrec * 3;
   const size_t hstep = (size_t)3 * c->geo.nmat;
+  const size_t sfloats = (size_t)fwi::kFields * c->geo.stride;
   if (hist) CUDA_TRY(c, cudaMemsetAsync(hist, 0, sizeof(float) * hstep, c->stream));
   fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces, c->stream);
   for (int n = 0; n < c->cfg.nsteps; n++) {
+    if (snap && n % every == 0)
+      CUDA_TRY(c, cudaMemcpyAsync(snap + (size_t)(n / every) * sfloats, c->state[0], sfloats * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, c->stream));
     TRY(rk4_step(c, false, n, shot, hist ? hist + (size_t)(n + 1) * hstep : nullptr));
     fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces + (n + 1) * per_step,
                        c->stream);
@@ -569,7 +581,11 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
 void fwi_destroy(fwi_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
-  for (int b = 0; b < 4; b++) dfree(c->state[b]);
+  for (int b = 0; b < 4; b++) {
+    dfree(c->state[b]);
+    dfree(c->rstate[b]);
+  }
+  dfree(c->d_snap);
   for (int ax = 0; ax < 3; ax++) {
     dfree(c->d_alpha[ax]);
     dfree(c->d_beta[ax]);
@@ -783,39 +799,94 @@ fwi_status run_misfit(fwi_ctx *c, int shot0, int nshots, const float *observed, 
 }
 
 // misfit and g_mis (dJ/dlambda_i, dJ/dmu_i) into d_gl / d_gm
+// (re)allocate the displacement history for `slots` levels
+fwi_status ensure_hist(fwi_ctx *c, size_t slots) {
+  if (c->hist_cap >= slots) return FWI_OK;
+  dfree(c->d_hist);
+  c->hist_cap = 0;
+  TRY(dalloc(c, &c->d_hist, slots * 3 * (size_t)c->geo.nmat));
+  c->hist_cap = slots;
+  return FWI_OK;
+}
+
+// the adjoint step that yields w(t_lvl), and the gradient integrand at that level
+// from the displacement history slot `hist_lvl`
+fwi_status adjoint_level(fwi_ctx *c, int lvl, const float *hist_lvl) {
+  const int N = c->cfg.nsteps;
+  TRY(rk4_step(c, true, N - lvl - 1, 0, nullptr));
+  if (lvl > 0) {
+    const double wn = (lvl == N) ? 0.5 : 1.0;
+    cudaEvent_t e0;
+    time_begin(c, &e0);
+    fwi::launch_gradient(c->geo, c->state[0], hist_lvl, wn * c->cfg.dt, c->d_gl, c->d_gm, c->stream);
+    time_end(c, e0, 1);
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  return FWI_OK;
+}
+
 fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed, int on_device, double *J) {
   TRY(ensure_trace_buffers(c));
   TRY(ensure_J(c, nshots));
   const size_t nmat = (size_t)c->geo.nmat;
-  const size_t hbytes = (size_t)(c->cfg.nsteps + 1) * 3 * nmat;
-  TRY(dalloc(c, &c->d_hist, hbytes));
+  const int N = c->cfg.nsteps;
+  const size_t hstep = 3 * nmat;
+  // checkpoint interval: 0 keeps every level of the displacement history
+  int every = c->ckpt < 0 ? (int)std::ceil(std::sqrt((double)N)) : c->ckpt;
+  if (every >= N) every = 0;
+  const int nseg = every > 0 ? (N + every - 1) / every : 0;
+  const size_t sfloats = (size_t)fwi::kFields * c->geo.stride;
+  TRY(ensure_hist(c, every > 0 ? (size_t)every + 1 : (size_t)N + 1));
+  if (every > 0) {
+    if (c->snap_cap < (size_t)nseg) {
+      dfree(c->d_snap);
+      c->snap_cap = 0;
+      TRY(dalloc(c, &c->d_snap, (size_t)nseg * sfloats));
+      c->snap_cap = nseg;
+    }
+    for (int b = 0; b < 4; b++) {
+      if (c->rstate[b]) continue;
+      TRY(dalloc(c, &c->rstate[b], sfloats));
+      // entries that no stage writes (history and stress off the PML, fixed faces, padding) stay zero
+      CUDA_TRY(c, cudaMemsetAsync(c->rstate[b], 0, sfloats * sizeof(float), c->stream));
+    }
+  }
   TRY(dalloc(c, &c->d_gl, nmat));
   TRY(dalloc(c, &c->d_gm, nmat));
   CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_gl, 0, sizeof(double) * nmat, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_gm, 0, sizeof(double) * nmat, c->stream));
-  const int N = c->cfg.nsteps;
-  const size_t hstep = 3 * nmat;
   for (int s = 0; s < nshots; s++) {
-    TRY(forward_sweep(c, shot0 + s, c->d_hist));
+    const int shot = shot0 + s;
+    TRY(forward_sweep(c, shot, every > 0 ? nullptr : c->d_hist, every > 0 ? c->d_snap : nullptr, every));
     fwi_status st;
     const float *obs = observed_for_shot(c, observed, on_device, s, &st);
     if (!obs) return st;
     TRY(misfit_of_traces(c, obs, s));
     // adjoint sweep in reversed time with the gradient time integral (C.1f)/(C.1g)
     TRY(zero_state(c));
-    for (int m = 0; m < N; m++) {
-      TRY(rk4_step(c, true, m, 0, nullptr));
-      const int lvl = N - m - 1;  // adjoint state now holds w(t_lvl)
-      if (lvl > 0) {
-        const double wn = (lvl == N) ? 0.5 : 1.0;
-        cudaEvent_t e0;
-        time_begin(c, &e0);
-        fwi::launch_gradient(c->geo, c->state[0], c->d_hist + (size_t)lvl * hstep, wn * c->cfg.dt, c->d_gl,
-                             c->d_gm, c->stream);
-        time_end(c, e0, 1);
-        CUDA_TRY(c, cudaGetLastError());
-      }
+    if (every == 0) {
+      for (int lvl = N - 1; lvl >= 0; lvl--) TRY(adjoint_level(c, lvl, c->d_hist + (size_t)lvl * hstep));
+      continue;
+    }
+    // checkpointed: segment g holds the steps [g every, min((g+1) every, N)). Its forward
+    // steps are recomputed from snapshot g in the second state set, writing the history
+    // levels g every + 1 .. of the segment; then the adjoint runs through those levels.
+    // The recomputed steps repeat the forward sweep's arithmetic exactly, so the
+    // gradient equals the one from the stored history bit for bit.
+    for (int g = nseg - 1; g >= 0; g--) {
+      const int L0 = g * every, L1 = std::min(L0 + every, N);
+      std::swap(c->state, c->rstate);
+      fwi_status rs = FWI_OK;
+      if (cudaMemcpyAsync(c->state[0], c->d_snap + (size_t)g * sfloats, sfloats * sizeof(float),
+                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        rs = fail(c, FWI_E_CUDA, "snapshot restore failed");
+      for (int n = L0; n < L1 && rs == FWI_OK; n++)
+        rs = rk4_step(c, false, n, shot, c->d_hist + (size_t)(n + 1 - L0) * hstep);
+      std::swap(c->state, c->rstate);
+      TRY(rs);
+      for (int lvl = std::min(L1, N - 1); lvl > L0; lvl--)
+        TRY(adjoint_level(c, lvl, c->d_hist + (size_t)(lvl - L0) * hstep));
     }
   }
   fwi::launch_check_finite(c->d_gl, (int64_t)nmat, c->d_flag, c->stream);
@@ -1083,6 +1154,12 @@ fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int
     CUDA_TRY(c, cudaMemsetAsync(c->state[2], 0, n * sizeof(float), c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
+  return FWI_OK;
+}
+
+fwi_status fwi_set_checkpointing(fwi_ctx *c, int interval) {
+  if (!c) return FWI_E_INVAL;
+  c->ckpt = interval;
   return FWI_OK;
 }
 

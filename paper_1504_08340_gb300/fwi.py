@@ -50,7 +50,7 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
-           "fwi_step_reset", "fwi_get_material")
+           "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing")
 
 _lib = None
 
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_step.argtypes = [P, P, I, C.POINTER(StepOpts), C.POINTER(StepInfo)]
     lib.fwi_step_reset.argtypes = [P]
     lib.fwi_get_material.argtypes = [P, P, P, I]
+    lib.fwi_set_checkpointing.argtypes = [P, I]
     for name in EXPORTS:
         if name not in ("fwi_destroy", "fwi_last_error", "fwi_status_string"):
             getattr(lib, name).restype = I
@@ -263,6 +264,11 @@ class Context:
             raise TypeError("state and rate must both be host or both be device arrays")
         self._check(self.lib.fwi_rhs(self.ptr, int(adjoint), ps, po, ds))
         return out
+
+    def set_checkpointing(self, interval):
+        """0: store u at every step; k > 0: snapshot every k steps and recompute;
+        k < 0: every ceil(sqrt(nsteps)) steps (fwi_set_checkpointing)."""
+        self._check(self.lib.fwi_set_checkpointing(self.ptr, int(interval)))
 
     def set_timing(self, enable=True):
         self._check(self.lib.fwi_set_timing(self.ptr, int(enable)))
