@@ -227,6 +227,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--inversion-steps", type=int, default=2,
                     help="iterations of Algorithm 2 (fwi_step) timed after the gradient benchmark (0: skip)")
+    ap.add_argument("--checkpoint", type=int, default=0, metavar="K",
+                    help="forward history of the adjoint: 0 stored every step, K > 0 snapshots every K "
+                         "steps with recompute, K < 0 every ceil(sqrt(nsteps)) steps")
     ap.add_argument("--profile-forward", type=int, default=0, metavar="NSTEPS",
                     help="profiling aid: run only short forward sweeps (NSTEPS RK4 steps) on the same mesh")
     args = ap.parse_args()
@@ -250,6 +253,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx, obs, (l0, m0) = setup(w, torch, dev)
+    ctx.set_checkpointing(args.checkpoint)
     gl = torch.empty(ctx.mat_shape(), dtype=torch.float64, device=dev)
     gm = torch.empty_like(gl)
 
@@ -341,6 +345,9 @@ def main():
                        "nodes": ctx.nnode, "elements": ctx.nelem, "nsteps": w.nsteps, "dt": w.dt,
                        "receivers": w.nrec_side ** 2, "shots_per_step_per_gpu": 1,
                        "parallelism": f"shot replicas x{world}",
+                       "forward_history": ("stored every step" if args.checkpoint == 0 else
+                                           f"checkpoint every {args.checkpoint if args.checkpoint > 0 else 'ceil(sqrt(N))'}"
+                                           " steps, recomputed"),
                        "l2": "inputs larger than L2 (1 GB state, 26 GB history per step)"},
             "element_stage_updates_per_s": value * elem_stage,
             "misfit": J,
