@@ -73,6 +73,8 @@ def _load():
         lib.orc_adjoint_gradient.argtypes = [P, C.c_double, C.c_int, C.c_int, L, D, D, D, D]
         lib.orc_gradient_term.argtypes = [P, D, D, C.c_double, D, D]
         lib.orc_energy.argtypes = [P, D, D]
+        lib.orc_regularization.argtypes = [P, C.c_int, C.c_double, D, D]
+        lib.orc_regularization.restype = C.c_double
         _lib = lib
         return lib
 
@@ -231,6 +233,16 @@ class Oracle:
         self.lib.orc_gradient_term(self.ptr, _d(np.ascontiguousarray(u, dtype=np.float64)),
                                    _d(np.ascontiguousarray(w, dtype=np.float64)), wdt, _d(gl), _d(gm))
         return gl, gm
+
+    def regularization(self, f, kind="tn", eps=0.0):
+        """(R, g): the TN (8) or TV (9) term of a field on the interior nodes and its
+        gradient (C.1b)-(C.1e), without the regularisation factor."""
+        f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        if f.size != self.nmat:
+            raise ValueError("field must have one value per interior node")
+        g = np.zeros(self.nmat)
+        R = self.lib.orc_regularization(self.ptr, {"tn": 0, "tv": 1}[kind], float(eps), _d(f), _d(g))
+        return R, g
 
     def misfit_and_gradient(self, dt, nsteps, src_nodes, src_dirs, rec_nodes, observed,
                             wavelet="ricker", wparams=(15.0, 0.1, 1e3)):

@@ -23,6 +23,8 @@
  *   Eq. (18), Appendix C (C.1a, C.1f, C.1g): misfit part of the lambda / mu
  *     gradients, restricted to the regular (interior) domain, and the lumped
  *     mass-like matrix Mtilde.
+ *   Eqs. (8), (9) with (C.1b)-(C.1e): Tikhonov and total-variation
+ *     regularisation terms and their gradients on the interior nodal field.
  *
  * Readings where the paper is silent, defers to its companion paper [13], or is
  * garbled (each is also listed in the design notes):
@@ -44,6 +46,11 @@
  *   R6 PML material is the value at the nearest interface node (index clamp),
  *      and the gradient is restricted to interior elements (Sec. 3.1.3).
  *   R7 (13b) writes "c S" where the adjoint stress T is meant; T is used.
+ *   R8 (17a)/(17b) and (C.1d)/(C.1e) are the derivative of
+ *      R int (|grad f|^2 + eps)^(1/2), i.e. of (9) without its factor 1/2; the TV
+ *      functional is taken as that, so that the gradient is its derivative. The
+ *      denominator of (C.1d)/(C.1e) is read pointwise: |grad f_h|^2 at the
+ *      quadrature point. TN (8) and (16), (C.1b)/(C.1c) agree as printed.
  *
  * Pins: see tests/test_oracle_*.py (stiffness symmetry and rigid modes, patch
  * test, transposes by the dot-product test, RK4 against the exact amplification
@@ -785,4 +792,55 @@ void orc_energy(orc_mesh *m, const double *Y, double *out) {
   for (long i = 0; i < n * 3; i++) es += 0.5 * u[i] * f[i];
   out[0] = ek; out[1] = es;
   free(u); free(f);
+}
+
+/* ---- regularisation, Sec. 3.1 Eqs. (8)/(9), gradients (C.1b)-(C.1e).
+ * f: a nodal field on the interior (material) grid [nmat], e.g. lambda or mu.
+ * For every interior element and quadrature point q (the element's 27 nodes):
+ *   grad f_h(q) from the element's nodal values (chi = the nodal Lagrange basis),
+ *   TN (kind 0): R += W detJ |grad f_h(q)|^2 / 2,
+ *                g_a += W detJ grad chi_a(q) . grad f_h(q)                  (C.1b/c)
+ *   TV (kind 1): R += W detJ (|grad f_h(q)|^2 + eps)^(1/2),
+ *                g_a += W detJ grad chi_a(q) . grad f_h(q) / (|grad f_h(q)|^2 + eps)^(1/2)
+ *                                                                  (C.1d/e, R8)
+ * without the factors R_lambda, R_mu. Plain serial element loop. g is overwritten. */
+static long mat_node_of(const orc_mesh *m, int ex, int ey, int ez, const int a[3]) {
+  int mx = 2 * m->nel[0] + 1, my = 2 * m->nel[1] + 1;
+  int i = 2 * (ex - m->lo[0]) + a[0], j = 2 * (ey - m->lo[1]) + a[1], k = 2 * (ez - m->lo[2]) + a[2];
+  return ((long)k * my + j) * mx + i;
+}
+
+double orc_regularization(const orc_mesh *m, int kind, double eps, const double *f, double *g) {
+  memset(g, 0, sizeof(double) * m->nmat);
+  double R = 0.0;
+  for (int ez = m->lo[2]; ez < m->hi[2]; ez++)
+    for (int ey = m->lo[1]; ey < m->hi[1]; ey++)
+      for (int ex = m->lo[0]; ex < m->hi[0]; ex++)
+        for (int cq = 0; cq < 27; cq++) {
+          int q[3] = {cq % 3, (cq / 3) % 3, cq / 9};
+          double gf[3] = {0.0, 0.0, 0.0};
+          for (int j = 0; j < 3; j++)
+            for (int b = 0; b < 3; b++) {
+              int a[3] = {q[0], q[1], q[2]};
+              a[j] = b;
+              gf[j] += dphi(m, a, q, j) * f[mat_node_of(m, ex, ey, ez, a)];
+            }
+          double s2 = gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2];
+          double wq = quad_weight(m, q);
+          double scale = 1.0;
+          if (kind == 1) {
+            double root = sqrt(s2 + eps);
+            R += wq * root;
+            scale = 1.0 / root;
+          } else {
+            R += 0.5 * wq * s2;
+          }
+          for (int j = 0; j < 3; j++)
+            for (int b = 0; b < 3; b++) {
+              int a[3] = {q[0], q[1], q[2]};
+              a[j] = b;
+              g[mat_node_of(m, ex, ey, ez, a)] += wq * dphi(m, a, q, j) * gf[j] * scale;
+            }
+        }
+  return R;
 }
