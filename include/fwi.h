@@ -66,6 +66,7 @@ typedef enum {
 } fwi_status;
 
 enum { FWI_WAVELET_RICKER = 0, FWI_WAVELET_GAUSS = 1 };
+enum { FWI_REG_TN = 0, FWI_REG_TV = 1 };  /* regularisation schemes, Eqs. (8) and (9) */
 
 typedef struct {
   int nx, ny, nz;   /* interior elements per axis (>= 1) */
@@ -184,6 +185,20 @@ fwi_status fwi_step(fwi_ctx *ctx, const float *observed, int on_device, const fw
 
 /* Forget the L-BFGS pairs (e.g. when the source wavelet changes, Sec. 3.3.2). */
 fwi_status fwi_step_reset(fwi_ctx *ctx);
+
+/* Regularisation term of the objective (7) at the context's material, Sec. 3.1:
+ * Tikhonov (kind FWI_REG_TN, Eq. (8)) or total variation (FWI_REG_TV, Eq. (9)),
+ * for lambda and for mu, without the factors R_lambda, R_mu:
+ *   R[0], R[1] (host): int |grad f|^2 / 2 (TN) or int (|grad f|^2 + eps)^(1/2) (TV)
+ *     over the interior domain, f = lambda, mu, by the LGL quadrature of the mesh;
+ *   g_lambda, g_mu (FP64, dims[4] values on the interior nodes, host or device per
+ *     on_device; either may be null): their gradients, g_reg of (18), as in
+ *     (C.1b)-(C.1e).
+ * The TV functional is the one whose derivative is (17a)/(C.1d): (9) without
+ * its factor 1/2. Errors: FWI_E_STATE (no material), FWI_E_INVAL (unknown kind,
+ * eps <= 0 for TV, null R). */
+fwi_status fwi_regularization(fwi_ctx *ctx, int kind, double eps, double *R, double *g_lambda, double *g_mu,
+                              int on_device);
 
 /* How fwi_adjoint_gradient and fwi_step give the adjoint sweep the forward
  * displacement u(t_n) that the gradient integrals (C.1f)/(C.1g) need at every step:

@@ -74,6 +74,8 @@ struct fwi_ctx {
   double *d_dir = nullptr, *d_S = nullptr, *d_Yv = nullptr, *d_opart = nullptr, *d_oscal = nullptr;
   unsigned *d_oflags = nullptr;
   unsigned long long *d_omax = nullptr;
+  // regularisation (fwi_regularization): gradients, block partials, functional values
+  double *d_rg = nullptr, *d_rpart = nullptr, *d_rval = nullptr;
 
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
@@ -610,7 +612,7 @@ void fwi_destroy(fwi_ctx *c) {
   dfree(c->d_gl);
   dfree(c->d_gm);
   for (double **p : {&c->d_mt, &c->d_m, &c->d_mprev, &c->d_g, &c->d_gprev, &c->d_dir, &c->d_S, &c->d_Yv,
-                     &c->d_opart, &c->d_oscal})
+                     &c->d_opart, &c->d_oscal, &c->d_rg, &c->d_rpart, &c->d_rval})
     dfree(*p);
   dfree(c->d_oflags);
   dfree(c->d_omax);
@@ -1154,6 +1156,33 @@ fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int
     CUDA_TRY(c, cudaMemsetAsync(c->state[2], 0, n * sizeof(float), c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
+  return FWI_OK;
+}
+
+fwi_status fwi_regularization(fwi_ctx *c, int kind, double eps, double *R, double *g_lambda, double *g_mu,
+                              int on_device) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (!c->have_material) return fail(c, FWI_E_STATE, "material not set");
+  if (kind != FWI_REG_TN && kind != FWI_REG_TV) return fail(c, FWI_E_INVAL, "unknown regularisation %d", kind);
+  if (kind == FWI_REG_TV && !(eps > 0)) return fail(c, FWI_E_INVAL, "total variation needs eps > 0");
+  if (!R) return fail(c, FWI_E_INVAL, "null R");
+  const size_t nmat = (size_t)c->geo.nmat;
+  TRY(dalloc(c, &c->d_rg, 2 * nmat));
+  TRY(dalloc(c, &c->d_rpart, 1024));
+  TRY(dalloc(c, &c->d_rval, 2));
+  const float *f[2] = {c->d_lam, c->d_mu};
+  double *out[2] = {g_lambda, g_mu};
+  for (int p = 0; p < 2; p++) {
+    double *g = (on_device && out[p]) ? out[p] : c->d_rg + p * nmat;
+    fwi::opt_regularization(f[p], c->geo.m, c->cfg.h, kind == FWI_REG_TV, eps, g, c->d_rpart, c->d_rval + p,
+                            c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    if (!on_device && out[p])
+      CUDA_TRY(c, cudaMemcpyAsync(out[p], g, nmat * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(R, c->d_rval, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return FWI_OK;
 }
 

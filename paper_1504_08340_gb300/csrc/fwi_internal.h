@@ -103,6 +103,10 @@ void opt_wdot(const double *a, const double *b, const double *w, int64_t nmat, d
 void opt_axpby(double *y, double a, const double *x, double b, int64_t n, cudaStream_t s);
 void opt_riesz(const double *gl, const double *gm, const double *mt, double *g, int64_t nmat, int mask,
                cudaStream_t s);
+// regularisation term (8)/(9) of a field on the material grid (m nodes per axis):
+// gradient (C.1b)-(C.1e) into g, functional into *value (device), part: >= 1024 doubles
+void opt_regularization(const float *f, const int m[3], double h, bool tv, double eps, double *g, double *part,
+                        double *value, cudaStream_t s);
 void opt_trial(const double *m, const double *d, double alpha, float *lam, float *mu, int64_t nmat, unsigned *flags,
                cudaStream_t s);
 void opt_pack(const float *lam, const float *mu, double *m, int64_t nmat, cudaStream_t s);

@@ -50,7 +50,7 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
-           "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing")
+           "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization")
 
 _lib = None
 
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_step_reset.argtypes = [P]
     lib.fwi_get_material.argtypes = [P, P, P, I]
     lib.fwi_set_checkpointing.argtypes = [P, I]
+    lib.fwi_regularization.argtypes = [P, I, C.c_double, D, P, P, I]
     for name in EXPORTS:
         if name not in ("fwi_destroy", "fwi_last_error", "fwi_status_string"):
             getattr(lib, name).restype = I
@@ -264,6 +265,23 @@ class Context:
             raise TypeError("state and rate must both be host or both be device arrays")
         self._check(self.lib.fwi_rhs(self.ptr, int(adjoint), ps, po, ds))
         return out
+
+    def regularization(self, kind="tn", eps=0.0, device=False):
+        """(R, g_lambda, g_mu): the TN (8) or TV (9) term of the current lambda and mu
+        (R = [R_lambda_term, R_mu_term], without the factors) and its gradients (C.1b)-(C.1e),
+        FP64 on the interior nodes (numpy, or torch CUDA tensors with device=True)."""
+        R = (C.c_double * 2)()
+        if device:
+            import torch
+            gl = torch.empty(self.mat_shape(), dtype=torch.float64, device="cuda")
+            gm = torch.empty_like(gl)
+        else:
+            gl = np.empty(self.mat_shape())
+            gm = np.empty(self.mat_shape())
+        pl, dl = _ptr(gl, np.float64)
+        pm, _ = _ptr(gm, np.float64)
+        self._check(self.lib.fwi_regularization(self.ptr, {"tn": 0, "tv": 1}[kind], float(eps), R, pl, pm, dl))
+        return [R[0], R[1]], gl, gm
 
     def set_checkpointing(self, interval):
         """0: store u at every step; k > 0: snapshot every k steps and recompute;
