@@ -157,6 +157,10 @@ typedef struct {
   double rho;         /* backtracking factor (Algorithm 1: 0.5) */
   int max_backtracks; /* trial steps before the iteration gives up */
   double first_step;  /* first trial update (no L-BFGS pairs yet): max|alpha d| = first_step * max|m| */
+  int reg;            /* regularisation of (7): -1 none (R = 0), FWI_REG_TN (8) or FWI_REG_TV (9) */
+  double reg_eps;     /* eps of (9) */
+  double reg_wp;      /* wp of (23c): each iteration R_p = wp |g_mis,p| / |g_reg,p| (24), p = lambda, mu */
+  double bias_w;      /* W of (25): the lambda search direction is biased toward mu's (0: no biasing) */
 } fwi_step_opts;
 
 typedef struct {
@@ -166,10 +170,15 @@ typedef struct {
   int trials;          /* misfit evaluations of the line search */
   int accepted;        /* 1 when the Armijo condition held and the material moved */
   int pairs;           /* L-BFGS pairs held after the iteration */
+  double R_lambda, R_mu; /* regularisation factors of the iteration (24) (0 without regularisation) */
+  double Jmis_old, Jmis_new; /* misfit parts of J_old, J_new */
 } fwi_step_info;
 
 /* One iteration of Algorithm 2 (lines 6-11) at the current material:
- * gradient (state (6), adjoint (15), g = Mtilde^-1 g_mis of (18) with R = 0),
+ * gradient (state (6), adjoint (15), g = Mtilde^-1 (R g_reg + g_mis) of (18); with
+ * opts->reg >= 0 the factors R_lambda, R_mu follow (24) from opts->reg_wp at the
+ * current material, and J_old, J_new are the misfit plus R_p times the terms of
+ * fwi_regularization: the objective (7) that the line search tests),
  * L-BFGS search direction (two-loop recursion in the Mtilde inner product,
  * <a, b> = sum_i a_i Mtilde_i b_i, so that <g, d> = g_mis . d is the exact
  * directional derivative), Armijo backtracking of Algorithm 1 (alpha^lambda =
@@ -177,9 +186,13 @@ typedef struct {
  * material. Trial materials that violate mu > 0, lambda + 2 mu > 0 or the time-step
  * limit count as failed trials. The L-BFGS pairs live on the device (FP64, 2 *
  * lbfgs_m vectors of 2 * dims[4] values) and persist between calls; a pair is kept
- * only when <s, y> > 0. observed: as fwi_misfit (host or device); info: host.
+ * only when <s, y> > 0. With opts->bias_w = W > 0 and invert = 3, the lambda part
+ * of the direction becomes |d_l| (W d_m / |d_m| + (1 - W) d_l / |d_l|) (25)
+ * (Euclidean norms; the unbiased direction is kept when the biased one is not a
+ * descent direction). observed: as fwi_misfit (host or device); info: host.
  * When no trial satisfies Armijo the material is restored, info->accepted = 0 and
- * the memory is cleared. Errors: as fwi_adjoint_gradient, FWI_E_INVAL (options). */
+ * the memory is cleared. Errors: as fwi_adjoint_gradient, FWI_E_INVAL (options:
+ * also reg outside -1..1, TV with reg_eps <= 0, reg_wp < 0, bias_w outside [0, 1]). */
 fwi_status fwi_step(fwi_ctx *ctx, const float *observed, int on_device, const fwi_step_opts *opts,
                     fwi_step_info *info);
 

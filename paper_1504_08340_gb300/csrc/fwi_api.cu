@@ -934,6 +934,30 @@ fwi_status wdot(fwi_ctx *c, const double *a, const double *b, double *out) {
   return FWI_OK;
 }
 
+fwi_status dot(fwi_ctx *c, const double *a, const double *b, int64_t n, double *out) {
+  fwi::opt_dot(a, b, n, c->d_opart, c->d_oscal, c->stream);
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->d_oscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
+// regularisation terms (8)/(9) of the context's lambda and mu into Rf[2]; with g, their
+// gradients into g (lambda half, then mu half)
+fwi_status reg_terms(fwi_ctx *c, int kind, double eps, double Rf[2], double *g) {
+  const size_t nmat = (size_t)c->geo.nmat;
+  TRY(dalloc(c, &c->d_rg, 2 * nmat));
+  TRY(dalloc(c, &c->d_rpart, 1024));
+  TRY(dalloc(c, &c->d_rval, 2));
+  const float *f[2] = {c->d_lam, c->d_mu};
+  for (int p = 0; p < 2; p++)
+    fwi::opt_regularization(f[p], c->geo.m, c->cfg.h, kind == FWI_REG_TV, eps, g ? g + p * nmat : c->d_rg + p * nmat,
+                            c->d_rpart, c->d_rval + p, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(Rf, c->d_rval, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
 fwi_status absmax(fwi_ctx *c, const double *x, double *out) {
   CUDA_TRY(c, cudaMemsetAsync(c->d_omax, 0, sizeof(unsigned long long), c->stream));
   fwi::opt_absmax(x, 2 * c->geo.nmat, c->d_omax, c->stream);
@@ -985,7 +1009,9 @@ fwi_status fwi_step(fwi_ctx *c, const float *observed, int on_device, const fwi_
   if (!o || !observed || !info) return fail(c, FWI_E_INVAL, "null argument");
   TRY(require_ready(c, o->shot0, o->nshots));
   if (o->invert < 1 || o->invert > 3 || o->lbfgs_m < 0 || o->lbfgs_m > 1000 || !(o->c1 > 0 && o->c1 < 1) ||
-      !(o->rho > 0 && o->rho < 1) || o->max_backtracks < 1 || !(o->first_step > 0))
+      !(o->rho > 0 && o->rho < 1) || o->max_backtracks < 1 || !(o->first_step > 0) || o->reg < -1 ||
+      o->reg > 1 || (o->reg == FWI_REG_TV && !(o->reg_eps > 0)) || !(o->reg_wp >= 0) ||
+      !(o->bias_w >= 0 && o->bias_w <= 1))
     return fail(c, FWI_E_INVAL, "invalid step options");
   const int64_t nmat = c->geo.nmat, n2 = 2 * nmat;
   // device vectors (allocated once; the pair store grows with lbfgs_m)
@@ -1014,6 +1040,24 @@ fwi_status fwi_step(fwi_ctx *c, const float *observed, int on_device, const fwi_
   // 1. misfit and gradient at the current material (Algorithm 2, lines 6-8)
   double J0 = 0.0;
   TRY(run_gradient(c, o->shot0, o->nshots, observed, on_device, &J0));
+  const double Jmis0 = J0;
+  double Rp[2] = {0.0, 0.0};  // regularisation factors R_lambda, R_mu of this iteration
+  if (o->reg >= 0) {
+    // (18): M g = R g_reg + g_mis with R_p = wp |g_mis,p| / |g_reg,p| (24)
+    double Rf[2];
+    TRY(reg_terms(c, o->reg, o->reg_eps, Rf, nullptr));
+    double *gmis[2] = {c->d_gl, c->d_gm};
+    for (int p = 0; p < 2; p++) {
+      if (!(o->invert & (1 << p))) continue;
+      double mm = 0.0, rr = 0.0;
+      TRY(dot(c, gmis[p], gmis[p], nmat, &mm));
+      TRY(dot(c, c->d_rg + p * nmat, c->d_rg + p * nmat, nmat, &rr));
+      Rp[p] = rr > 0.0 ? o->reg_wp * std::sqrt(mm) / std::sqrt(rr) : 0.0;
+      fwi::opt_axpby(gmis[p], Rp[p], c->d_rg + p * nmat, 1.0, nmat, c->stream);
+      J0 += Rp[p] * Rf[p];
+    }
+    CUDA_TRY(c, cudaGetLastError());
+  }
   fwi::opt_pack(c->d_lam, c->d_mu, c->d_m, nmat, c->stream);
   fwi::opt_riesz(c->d_gl, c->d_gm, c->d_mt, c->d_g, nmat, o->invert, c->stream);
   CUDA_TRY(c, cudaGetLastError());
@@ -1067,12 +1111,30 @@ fwi_status fwi_step(fwi_ctx *c, const float *observed, int on_device, const fwi_
     fwi::opt_axpby(c->d_dir, 0.0, c->d_dir, -1.0, n2, c->stream);
     CUDA_TRY(c, cudaGetLastError());
     TRY(wdot(c, c->d_g, c->d_dir, &gtd));
+    if (o->bias_w > 0.0 && o->invert == 3 && gtd < 0.0 && std::isfinite(gtd)) {
+      // (25): d_l <- |d_l| (W d_m / |d_m| + (1 - W) d_l / |d_l|), kept only if still a descent direction
+      double ll = 0.0, mm = 0.0;
+      TRY(dot(c, c->d_dir, c->d_dir, nmat, &ll));
+      TRY(dot(c, c->d_dir + nmat, c->d_dir + nmat, nmat, &mm));
+      if (ll > 0.0 && mm > 0.0) {
+        TRY(dalloc(c, &c->d_rg, 2 * nmat));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_rg, c->d_dir, sizeof(double) * nmat, cudaMemcpyDeviceToDevice, c->stream));
+        fwi::opt_axpby(c->d_dir, o->bias_w * std::sqrt(ll) / std::sqrt(mm), c->d_dir + nmat, 1.0 - o->bias_w, nmat,
+                       c->stream);
+        double gtb = 0.0;
+        TRY(wdot(c, c->d_g, c->d_dir, &gtb));
+        if (gtb < 0.0 && std::isfinite(gtb))
+          gtd = gtb;
+        else  // not a descent direction: back to the unbiased one
+          CUDA_TRY(c, cudaMemcpyAsync(c->d_dir, c->d_rg, sizeof(double) * nmat, cudaMemcpyDeviceToDevice, c->stream));
+      }
+    }
     if (gtd < 0.0 && std::isfinite(gtd)) break;
     c->lb_count = c->lb_head = 0;  // not a descent direction: drop the memory, steepest descent
     if (attempt == 1) return fail(c, FWI_E_NONFINITE, "no descent direction");
   }
   // 4. Armijo backtracking (Algorithm 1) and update (19)
-  double alpha = 1.0, J1 = J0;
+  double alpha = 1.0, J1 = J0, Jmis1 = Jmis0;
   int trials = 0, accepted = 0;
   for (int b = 0; b <= o->max_backtracks; b++, alpha *= o->rho) {
     int ok = 0;
@@ -1083,8 +1145,15 @@ fwi_status fwi_step(fwi_ctx *c, const float *observed, int on_device, const fwi_
     fwi_status st = run_misfit(c, o->shot0, o->nshots, observed, on_device, &Jt);
     if (st == FWI_E_NONFINITE) continue;
     TRY(st);
+    const double Jmis_t = Jt;
+    if (o->reg >= 0) {
+      double Rf[2];
+      TRY(reg_terms(c, o->reg, o->reg_eps, Rf, nullptr));
+      Jt += Rp[0] * Rf[0] + Rp[1] * Rf[1];
+    }
     if (Jt < J0 + o->c1 * alpha * gtd) {
       J1 = Jt;
+      Jmis1 = Jmis_t;
       accepted = 1;
       break;
     }
@@ -1107,6 +1176,10 @@ fwi_status fwi_step(fwi_ctx *c, const float *observed, int on_device, const fwi_
   info->trials = trials;
   info->accepted = accepted;
   info->pairs = c->lb_count;
+  info->R_lambda = Rp[0];
+  info->R_mu = Rp[1];
+  info->Jmis_old = Jmis0;
+  info->Jmis_new = Jmis1;
   return FWI_OK;
 }
 

@@ -103,6 +103,8 @@ void opt_wdot(const double *a, const double *b, const double *w, int64_t nmat, d
 void opt_axpby(double *y, double a, const double *x, double b, int64_t n, cudaStream_t s);
 void opt_riesz(const double *gl, const double *gm, const double *mt, double *g, int64_t nmat, int mask,
                cudaStream_t s);
+// plain dot product of n values (fixed-order reduction), part: >= 1024 doubles
+void opt_dot(const double *a, const double *b, int64_t n, double *part, double *out, cudaStream_t s);
 // regularisation term (8)/(9) of a field on the material grid (m nodes per axis):
 // gradient (C.1b)-(C.1e) into g, functional into *value (device), part: >= 1024 doubles
 void opt_regularization(const float *f, const int m[3], double h, bool tv, double eps, double *g, double *part,

@@ -28,6 +28,19 @@ __global__ void __launch_bounds__(kT) wdot_kernel(const double *a, const double 
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+__global__ void __launch_bounds__(kT) dot_kernel(const double *a, const double *b, int64_t n, double *part) {
+  __shared__ double sh[kT];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) acc += a[i] * b[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = kT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
 __global__ void __launch_bounds__(kT) sum_parts(const double *part, int nb, double *out) {
   __shared__ double sh[kT];
   double acc = 0.0;
@@ -217,6 +230,12 @@ void opt_wdot(const double *a, const double *b, const double *w, int64_t nmat, d
               cudaStream_t s) {
   const int nb = grid_for(2 * nmat);
   wdot_kernel<<<nb, kT, 0, s>>>(a, b, w, nmat, part);
+  sum_parts<<<1, kT, 0, s>>>(part, nb, out);
+}
+
+void opt_dot(const double *a, const double *b, int64_t n, double *part, double *out, cudaStream_t s) {
+  const int nb = grid_for(n);
+  dot_kernel<<<nb, kT, 0, s>>>(a, b, n, part);
   sum_parts<<<1, kT, 0, s>>>(part, nb, out);
 }
 

@@ -37,12 +37,14 @@ class StepOpts(C.Structure):
     """fwi_step_opts: one iteration of Algorithm 2 (L-BFGS + Armijo backtracking)."""
     _fields_ = [("shot0", C.c_int), ("nshots", C.c_int), ("invert", C.c_int), ("lbfgs_m", C.c_int),
                 ("c1", C.c_double), ("rho", C.c_double), ("max_backtracks", C.c_int),
-                ("first_step", C.c_double)]
+                ("first_step", C.c_double), ("reg", C.c_int), ("reg_eps", C.c_double), ("reg_wp", C.c_double),
+                ("bias_w", C.c_double)]
 
 
 class StepInfo(C.Structure):
     _fields_ = [("J_old", C.c_double), ("J_new", C.c_double), ("alpha", C.c_double), ("gtd", C.c_double),
-                ("trials", C.c_int), ("accepted", C.c_int), ("pairs", C.c_int)]
+                ("trials", C.c_int), ("accepted", C.c_int), ("pairs", C.c_int), ("R_lambda", C.c_double),
+                ("R_mu", C.c_double), ("Jmis_old", C.c_double), ("Jmis_new", C.c_double)]
 
 
 # every symbol the header declares; the CPU test checks the library exports them all
@@ -226,10 +228,13 @@ class Context:
         return J.value, g_lambda, g_mu
 
     def step(self, observed, shot0=0, nshots=1, invert=3, lbfgs_m=15, c1=1e-4, rho=0.5, max_backtracks=20,
-             first_step=0.05):
-        """One iteration of Algorithm 2; returns the StepInfo (J_old, J_new, alpha, ...)."""
+             first_step=0.05, reg=None, reg_eps=0.0, reg_wp=0.5, bias_w=0.0):
+        """One iteration of Algorithm 2; returns the StepInfo (J_old, J_new, alpha, ...).
+        reg: None, "tn" or "tv" (objective (7) with (8) or (9), factors from (24) with wp = reg_wp);
+        bias_w: W of the lambda search-direction biasing (25)."""
         p, dev = _ptr(observed, np.float32)
-        opts = StepOpts(shot0, nshots, invert, lbfgs_m, c1, rho, max_backtracks, first_step)
+        opts = StepOpts(shot0, nshots, invert, lbfgs_m, c1, rho, max_backtracks, first_step,
+                        {None: -1, "tn": 0, "tv": 1}[reg], reg_eps, reg_wp, bias_w)
         info = StepInfo()
         self._check(self.lib.fwi_step(self.ptr, p, dev, C.byref(opts), C.byref(info)))
         return info

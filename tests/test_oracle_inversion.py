@@ -58,3 +58,50 @@ def test_inversion_decreases_the_misfit(oracle_mod):
         Js.append((info["J_old"], info["J_new"]))
     assert Js[0][1] < Js[0][0] and Js[-1][1] < Js[0][0]
     assert all(b[0] == pytest.approx(a[1], rel=1e-12) for a, b in zip(Js, Js[1:]))
+
+
+def test_bias_direction_limits():
+    """(25): W = 0 leaves the direction alone; W = 1 points the lambda part along the
+    mu part with the lambda part's length; the mu part never changes."""
+    rng = np.random.default_rng(2)
+    n = 5
+    d = rng.standard_normal(2 * n)
+    assert np.allclose(inversion.bias_direction(d, n, 0.0), d, rtol=1e-14, atol=0)
+    d1 = inversion.bias_direction(d, n, 1.0)
+    assert np.allclose(d1[:n], np.linalg.norm(d[:n]) * d[n:] / np.linalg.norm(d[n:]), rtol=1e-14)
+    assert np.array_equal(d1[n:], d[n:])
+    dh = inversion.bias_direction(d, n, 0.5)
+    assert np.allclose(dh[:n], 0.5 * d1[:n] + 0.5 * d[:n], rtol=1e-14)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("reg,eps", [("tn", 0.0), ("tv", 0.01)])
+def test_regularized_inversion_decreases_the_objective(oracle_mod, reg, eps):
+    """Algorithm 2 with the regularised objective, R from (24) and lambda biasing (25):
+    every accepted step satisfies Armijo on J + R_l R^l + R_m R^m, and R_p is wp times
+    the ratio of the gradient norms (so the regularisation part is wp times the misfit part)."""
+    w = fi.tiny(nx=3, ny=3, nz=2, npml=2, nsteps=40, f0=30.0, nrec_side=3)
+    o = oracle_mod.Oracle(w.nx, w.ny, w.nz, w.npml, h=w.h, rho=w.rho)
+    lt, mt = (np.asarray(a, dtype=np.float32).astype(np.float64) for a in fi.medium(w, "true"))
+    l0, m0 = (np.asarray(a, dtype=np.float32).astype(np.float64) for a in fi.medium(w, "trial"))
+    src = [o.node_id(*s) for s in w.sources()]
+    rec = [o.node_id(*r) for r in w.receivers()]
+    o.set_material(lt, mt)
+    obs = o.forward(w.dt, w.nsteps, src, w.source_dirs(), "ricker", w.ricker(), rec)
+    # a trial model with structure, so that g_reg is not zero
+    rng = np.random.default_rng(9)
+    l0 = (l0.ravel() * (1 + 0.05 * rng.standard_normal(l0.size))).astype(np.float32).astype(np.float64)
+    m0 = (m0.ravel() * (1 + 0.05 * rng.standard_normal(m0.size))).astype(np.float32).astype(np.float64)
+    inv = inversion.Inversion(o, w.dt, w.nsteps, src, w.source_dirs(), rec, obs, "ricker", w.ricker(),
+                              reg=reg, reg_eps=eps, reg_wp=0.5, bias_w=0.5)
+    m = np.concatenate([l0, m0])
+    for _ in range(2):
+        mk = m.copy()
+        m, info = inv.step(m)
+        assert info["accepted"] == 1
+        assert info["J_new"] < info["J_old"] + 1e-4 * info["alpha"] * info["gtd"]
+        assert all(r > 0 for r in info["R"])
+        # the regularisation part of J_old is R_p times the terms at the start model
+        n = mk.size // 2
+        reg_part = sum(info["R"][p] * o.regularization(mk[p * n:(p + 1) * n], reg, eps)[0] for p in range(2))
+        assert info["J_old"] == pytest.approx(info["Jmis_old"] + reg_part, rel=1e-12)
