@@ -353,7 +353,7 @@ def main():
             "misfit": J,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": measured_traffic(w.name),
-                         "kernel": "RK4 stage (interior_kernel + pml_kernel + shell_kernel + pml_face_kernel, one launch set)", "peak_kind": peak_kind,
+                         "kernel": "RK4 stage (interior_kernel + shell_kernel + pml_face_kernel + pml_kernel stress and displacement parts, one launch set)", "peak_kind": peak_kind,
                          "bytes_per_launch": bytes_step / 4.0,
                          "avg_launch_ms": stage_ms / max(stage_launches, 1),
                          "stage_share_of_step": stage_ms / (ms * args.steps) if ms > 0 else None},

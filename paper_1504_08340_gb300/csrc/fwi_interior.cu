@@ -321,12 +321,13 @@ cudaError_t prepare_interior() {
   return cudaFuncSetAttribute(interior_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
 }
 
-void launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s) {
-  if (g.box_hi[0] < g.box_lo[0] || g.box_hi[1] < g.box_lo[1] || g.box_hi[2] < g.box_lo[2]) return;
+int launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s) {
+  if (g.box_hi[0] < g.box_lo[0] || g.box_hi[1] < g.box_lo[1] || g.box_hi[2] < g.box_lo[2]) return 0;
   const int nx = g.box_hi[0] - (g.box_lo[0] - 1) + 1;
   const dim3 grd((nx + 2 * kTP - 1) / (2 * kTP), (g.box_hi[1] - g.box_lo[1] + kTY) / kTY,
                  (g.box_hi[2] - g.box_lo[2] + kKC) / kKC);
   interior_kernel<<<grd, dim3(kTP, kTY), kSmem, s>>>(g, a);
+  return 1;
 }
 
 }  // namespace fwi

@@ -48,16 +48,18 @@ struct StageArgs {
   float *hist;       // stage 4: interior displacement written here as [3][nmat], or null
 };
 
-// One RK4 stage is four kernels writing disjoint node sets; they read the same
-// input and may run concurrently on different streams:
+// One RK4 stage is five kernels writing disjoint node sets; they read the same
+// input and may run concurrently on different streams. Each launcher returns the
+// number of kernels it launched:
 //  launch_interior: nodes all of whose elements are interior (fwi_interior.cu);
-//  launch_pml:      nodes all of whose elements are PML, off the outer faces (fwi_pml.cu);
+//  launch_pml:      nodes all of whose elements are PML, off the outer faces (fwi_pml.cu;
+//                   two kernels: the stress rows, then the displacement rows);
 //  launch_shell:    the interface shell (fwi_stage.cu) and the PML nodes on the
 //                   outer faces of the grid (launch_pml_face, fwi_pml.cu).
-void launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s);
-void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
-void launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
-void launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+int launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s);
+int launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+int launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
+int launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s);
 // raises the interior kernel's shared-memory limit on the current device
 cudaError_t prepare_interior();
 

@@ -23,6 +23,8 @@
 // (outside the closed interior box), with 32-bit field offsets.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fwi_internal.h"
 
 namespace fwi {
@@ -234,15 +236,17 @@ __device__ __forceinline__ void adj_yz(const Geo &g, const float *__restrict__ Y
   }
 }
 
-template <bool ADJ, int MODE, int KY, int KZ>
+// PART 0: the whole pair update; 1: the stress rows only; 2: the displacement rows only
+template <bool ADJ, int MODE, int KY, int KZ, int PART = 0>
 __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K, bool even_ok) {
+  constexpr bool DO_S = PART != 2, DO_U = PART != 1;
   const int S = (int)g.stride;
   const int node = (K * g.n[1] + J) * g.px + I0;
   const int sy = g.px, sz = g.px * g.n[1];
   const float *__restrict__ Yn = a.Y + node;
   const Coef2 cf = coef_pair(g, I0, J, K);
   float2 f[3] = {bc(0.f), bc(0.f), bc(0.f)};  // u-row sums (times h)
-  if constexpr (ADJ) {
+  if constexpr (ADJ && DO_U) {
     // Q = sum_lv Lambda^lv_jj tau(T^lv): pointwise with the material of each line point.
     // x: Q at the points I0-2 .. I0+3 as three aligned pairs (the last point is not
     // used); even node (LR): 0.5 Q[-2] - 2 Q[-1] + 2 Q[+1] - 0.5 Q[+2], odd node (C,
@@ -264,7 +268,7 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
   }
   // ---- S rows: H_ij = sum_lv Lambda^lv_jj D_j u^lv_i (times h)
   float2 s[6];
-  {
+  if constexpr (DO_S) {
     float2 H[3][3];  // [i][j]
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -284,7 +288,7 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
     s[0] = H[0][0]; s[1] = H[1][1]; s[2] = H[2][2];
     s[3] = padd(H[1][2], H[2][1]); s[4] = padd(H[0][2], H[2][0]); s[5] = padd(H[0][1], H[1][0]);
   }
-  if constexpr (!ADJ) {  // tau(P(H)) with the node's own material
+  if constexpr (!ADJ && DO_S) {  // tau(P(H)) with the node's own material
     const int me = mat_at(g, I0, J, K), mo = mat_at(g, I0 + 1, J, K);
     const float2 lm = make_float2(__ldg(g.lam + me), __ldg(g.lam + mo));
     const float2 mu = make_float2(__ldg(g.mu + me), __ldg(g.mu + mo));
@@ -299,8 +303,9 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
   // ---- u rows (times h): f_c = sum_j D_j Q_cj; forward Q = sum_lv Lambda^lv_jj S^lv
   const float2 ih = bc(g.inv_h);
   // S components in the order xx yy zz yz xz xy; for each: (c, j) pairs it feeds
+  constexpr bool PHASE_B = DO_S || !ADJ;  // the adjoint u rows need nothing from this loop
 #pragma unroll
-  for (int comp = 0; comp < 6; comp++) {
+  for (int comp = 0; comp < (PHASE_B ? 6 : 0); comp++) {
     float2 sv[3];  // own values per level
 #pragma unroll
     for (int lv = 0; lv < 3; lv++) {
@@ -308,17 +313,15 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
       const bool on_x = comp == 0 || comp == 4 || comp == 5;  // xx, xz, xy
       const bool on_y = comp == 1 || comp == 3 || comp == 5;  // yy, yz, xy
       const bool on_z = comp == 2 || comp == 3 || comp == 4;  // zz, yz, xz
-      if (on_x) {
+      if (on_x && !ADJ && DO_U) {
         const XWin w = xwin(p);
         sv[lv] = make_float2(w.v[2], w.v[3]);
-        if constexpr (!ADJ) {
-          const int c = comp == 0 ? 0 : (comp == 5 ? 1 : 2);  // xx -> c 0, xy -> c 1, xz -> c 2 (j = x)
-          f[c] = pfma(bc(cf.Lx[lv]), dx2(w), f[c]);
-        }
-      } else {
+        const int c = comp == 0 ? 0 : (comp == 5 ? 1 : 2);  // xx -> c 0, xy -> c 1, xz -> c 2 (j = x)
+        f[c] = pfma(bc(cf.Lx[lv]), dx2(w), f[c]);
+      } else if (DO_S) {
         sv[lv] = ld2(p);
       }
-      if constexpr (!ADJ) {
+      if constexpr (!ADJ && DO_U) {
         if (on_y) {
           const int c = comp == 1 ? 1 : (comp == 5 ? 0 : 2);  // yy -> 1, xy -> 0, yz -> 2 (j = y)
           f[c] = pfma(cf.Ly[lv], dline<KY>(p, sy), f[c]);
@@ -329,6 +332,7 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
         }
       }
     }
+    if constexpr (!DO_S) continue;
     // stress update of this component: S'' = (src - b S' - c S - d Sbar) / a
     const int i0 = (3 + comp) * S + node, i1 = (12 + comp) * S + node, i2 = (21 + comp) * S + node;
     const float2 acc = pmul(pfma(cf.nb, sv[2], pfma(cf.nc, sv[1], pfma(cf.nd, sv[0], pmul(s[comp], ih)))), cf.ia);
@@ -338,6 +342,7 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
   }
   // ---- displacement update: u'' = (f / h) / (rho a) - (b u' + c u + d ubar) / a
   // (own u values read again here rather than held since the S rows)
+  if constexpr (!DO_U) return;
   const float2 irh = bc(g.inv_rho_h);
 #pragma unroll
   for (int c = 0; c < 3; c++) {
@@ -508,6 +513,9 @@ __device__ __forceinline__ void face_write(const Geo &g, const StageArgs &a, con
   }
 }
 
+#ifndef FWI_PML_SPLIT_MINB
+#define FWI_PML_SPLIT_MINB 8
+#endif
 #ifndef FWI_PML_BY
 #define FWI_PML_BY 4
 #endif
@@ -521,8 +529,9 @@ constexpr int kBX = 32, kBY = FWI_PML_BY;
 
 // grid.x: blocks of kBY warp tasks (see Region); tasks of a box run plane by plane.
 // The boxes exclude the outer faces of the grid, so every node takes the bulk path.
-template <bool ADJ, int MODE>
-__global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, StageArgs a, Region r) {
+template <bool ADJ, int MODE, int PART>
+__global__ void __launch_bounds__(kBX *kBY, PART == 0 ? FWI_PML_MINB : FWI_PML_SPLIT_MINB)
+    pml_kernel(Geo g, StageArgs a, Region r) {
   const int task = blockIdx.x * kBY + threadIdx.y;
   if (task >= r.tasks_before[r.nbox]) return;
   int b = 0;
@@ -550,11 +559,11 @@ __global__ void __launch_bounds__(kBX *kBY, FWI_PML_MINB) pml_kernel(Geo g, Stag
     // the even node of a box's first pair may not be (its results are dropped)
     const bool even_ok = I0 >= r.lo[b][0];
     if (ky == kSC) {
-      if (kz == kSC) pml_pair<ADJ, MODE, kSC, kSC>(g, a, I0, J, K, even_ok);
-      else pml_pair<ADJ, MODE, kSC, kSLR>(g, a, I0, J, K, even_ok);
+      if (kz == kSC) pml_pair<ADJ, MODE, kSC, kSC, PART>(g, a, I0, J, K, even_ok);
+      else pml_pair<ADJ, MODE, kSC, kSLR, PART>(g, a, I0, J, K, even_ok);
     } else {
-      if (kz == kSC) pml_pair<ADJ, MODE, kSLR, kSC>(g, a, I0, J, K, even_ok);
-      else pml_pair<ADJ, MODE, kSLR, kSLR>(g, a, I0, J, K, even_ok);
+      if (kz == kSC) pml_pair<ADJ, MODE, kSLR, kSC, PART>(g, a, I0, J, K, even_ok);
+      else pml_pair<ADJ, MODE, kSLR, kSLR, PART>(g, a, I0, J, K, even_ok);
     }
   }
 }
@@ -625,33 +634,42 @@ static Region pml_region(const Geo &g) {
   return r;
 }
 
-void launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
+int launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
   const Region r = pml_region(g);
   const int tasks = r.tasks_before[r.nbox];
-  if (tasks == 0) return;
+  if (tasks == 0) return 0;
   const dim3 grd((tasks + kBY - 1) / kBY), blk(kBX, kBY);
   const int mode = a.stage == 0 ? 0 : (a.stage == 1 ? 1 : (a.stage < 4 ? 2 : 3));
-  if (adjoint) {
-    if (mode == 0) pml_kernel<true, 0><<<grd, blk, 0, s>>>(g, a, r);
-    else if (mode == 1) pml_kernel<true, 1><<<grd, blk, 0, s>>>(g, a, r);
-    else if (mode == 2) pml_kernel<true, 2><<<grd, blk, 0, s>>>(g, a, r);
-    else pml_kernel<true, 3><<<grd, blk, 0, s>>>(g, a, r);
-  } else {
-    if (mode == 0) pml_kernel<false, 0><<<grd, blk, 0, s>>>(g, a, r);
-    else if (mode == 1) pml_kernel<false, 1><<<grd, blk, 0, s>>>(g, a, r);
-    else if (mode == 2) pml_kernel<false, 2><<<grd, blk, 0, s>>>(g, a, r);
-    else pml_kernel<false, 3><<<grd, blk, 0, s>>>(g, a, r);
-  }
+  auto go = [&](auto part, cudaStream_t st) {
+    constexpr int P = decltype(part)::value;
+    if (adjoint) {
+      if (mode == 0) pml_kernel<true, 0, P><<<grd, blk, 0, st>>>(g, a, r);
+      else if (mode == 1) pml_kernel<true, 1, P><<<grd, blk, 0, st>>>(g, a, r);
+      else if (mode == 2) pml_kernel<true, 2, P><<<grd, blk, 0, st>>>(g, a, r);
+      else pml_kernel<true, 3, P><<<grd, blk, 0, st>>>(g, a, r);
+    } else {
+      if (mode == 0) pml_kernel<false, 0, P><<<grd, blk, 0, st>>>(g, a, r);
+      else if (mode == 1) pml_kernel<false, 1, P><<<grd, blk, 0, st>>>(g, a, r);
+      else if (mode == 2) pml_kernel<false, 2, P><<<grd, blk, 0, st>>>(g, a, r);
+      else pml_kernel<false, 3, P><<<grd, blk, 0, st>>>(g, a, r);
+    }
+  };
+  // two launches: the stress rows, then the displacement rows (disjoint outputs, the same
+  // inputs). Each needs fewer registers than the whole update, so more warps are resident.
+  go(std::integral_constant<int, 1>{}, s);
+  go(std::integral_constant<int, 2>{}, s);
+  return 2;
 }
 
-void launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
-  if (g.nface <= 0) return;
+int launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
+  if (g.nface <= 0) return 0;
   const int nb = (g.nface + kFaceNodes - 1) / kFaceNodes;
   const dim3 blk(kFaceNodes, 3);
   if (adjoint)
     pml_face_kernel<true><<<nb, blk, 0, s>>>(g, a);
   else
     pml_face_kernel<false><<<nb, blk, 0, s>>>(g, a);
+  return 1;
 }
 
 }  // namespace fwi

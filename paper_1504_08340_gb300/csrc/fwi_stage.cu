@@ -445,8 +445,10 @@ __global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(
 
 }  // namespace
 
-void launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
+int launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
+  int n = 0;
   if (g.nshell > 0) {
+    n = 1;
     const int nb = (g.nshell + kShellNodes - 1) / kShellNodes;
     const dim3 blk(kShellNodes, 3);
     if (adjoint)
@@ -454,7 +456,7 @@ void launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s
     else
       shell_kernel<false><<<nb, blk, 0, s>>>(g, a);
   }
-  launch_pml_face(g, a, adjoint, s);
+  return n + launch_pml_face(g, a, adjoint, s);
 }
 
 }  // namespace fwi
