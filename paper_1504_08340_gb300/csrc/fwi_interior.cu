@@ -13,10 +13,12 @@
 // c(q) = w_q (2/h) D[q][a] the line quadrature coefficient.
 //
 // GB300 mapping: a block owns a 64 x 8 node tile in (x, y) and marches along
-// z through a chunk of planes. u (3 components), lambda and mu of planes
-// K-2 .. K+2 sit in a shared-memory ring (6 planes x 5 fields x 12 rows x 68,
-// 97.9 KB); plane K+3 streams in with cp.async while plane K is computed. Each
-// thread computes a pair of nodes (even x, odd x) of plane K.
+// z through a chunk of planes. u (3 components) of planes K-2 .. K+2 sits in a
+// shared-memory ring (6 planes x 3 fields x 12 rows x 72 floats, 62.2 KB; rows
+// start at a 16-byte aligned x and are copied in 16-byte chunks); plane K+3
+// streams in with cp.async while plane K is computed. lambda and mu are read from
+// global memory (L1/L2 resident). Each thread computes a pair of nodes (even x,
+// odd x) of plane K.
 // Side types are template parameters, so every stencil access is a shared
 // load at a compile-time offset from one of five plane base registers.
 #include <cuda_runtime.h>
@@ -34,13 +36,13 @@ constexpr int kTP = 32;             // node pairs per tile row (64 nodes)
 #define FWI_INT_KC 8
 #endif
 constexpr int kTY = FWI_INT_TY;     // rows per tile
-constexpr int kTXS = 2 * kTP + 4;   // smem row pitch (halo 2 on each side)
+// smem row: the tile's 64 nodes with a halo of 2 on each side, from a 16-byte aligned
+// start (at most 2 nodes before the halo), copied in 16-byte chunks
+constexpr int kTXS = 2 * kTP + 8;   // smem row pitch
+constexpr int kCPR = kTXS / 4;      // 16-byte chunks per row
 constexpr int kTYS = kTY + 4;
 constexpr int kFS = kTXS * kTYS;    // floats per field and plane
-#ifndef FWI_INT_MAT_SMEM
-#define FWI_INT_MAT_SMEM 0
-#endif
-constexpr int kNF = FWI_INT_MAT_SMEM ? 5 : 3;  // u_x, u_y, u_z (, lambda, mu)
+constexpr int kNF = 3;              // u_x, u_y, u_z
 constexpr int kPS = kNF * kFS;      // floats per plane
 constexpr int kRing = 6;            // planes K-2 .. K+2 in use, K+3 in flight
 constexpr int kSmem = kRing * kPS * (int)sizeof(float);
@@ -59,7 +61,6 @@ struct Tile {
   int mi, ms1, ms2;       // material index of the node, material row / plane strides
   template <int DX, int DY, int DZ>
   __device__ __forceinline__ float mat(int which) const {
-    if constexpr (FWI_INT_MAT_SMEM) return v<DX, DY, DZ>(3 + which);
     return __ldg((which == 0 ? lam : mu) + mi + DX + DY * ms1 + DZ * ms2);
   }
   template <int DX, int DY, int DZ>
@@ -228,36 +229,27 @@ __device__ __forceinline__ void finish_node(const Geo &g, const StageArgs &a, in
   }
 }
 
-// asynchronous 4-byte global -> shared copy; src_bytes = 0 writes a zero
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
+// asynchronous 16-byte global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, int src_bytes) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// issue the copies of plane K (u of the stage input, lambda, mu) of the tile into dst
-__device__ __forceinline__ void load_plane(const Geo &g, const StageArgs &a, float *dst, int K, int x0, int y0) {
+// issue the copies of plane K (u of the stage input) of the tile into dst: rows
+// y0-2 .. y0+kTY+1, x from xs = (x0 - 2) rounded down to a multiple of 4. Chunks
+// outside the grid (rows, planes, x < 0 or x >= px) are zero-filled; the row padding
+// x in [NI, px) holds zeros in every state buffer.
+__device__ __forceinline__ void load_plane(const Geo &g, const StageArgs &a, float *dst, int K, int xs, int y0) {
   const int64_t S = g.stride;
   const bool kin = K >= 0 && K < g.n[2];
-  const int kk = K - 2 * g.lo[2];
-  const int kc = kk < 0 ? 0 : (kk >= g.m[2] ? g.m[2] - 1 : kk);
-  for (int idx = threadIdx.y * kTP + threadIdx.x; idx < kPS; idx += kTP * kTY) {
-    const int f = idx / kFS, r = (idx / kTXS) % kTYS, cx = idx % kTXS;
-    const int gx = x0 - 2 + cx, gy = y0 - 2 + r;
-    const bool ok = kin && gx >= 0 && gx < g.n[0] && gy >= 0 && gy < g.n[1];
-    const float *src = a.Y;
-    if (ok) {
-      if (f < 3) {
-        src = a.Y + (int64_t)(9 + f) * S + ((int64_t)K * g.n[1] + gy) * g.px + gx;
-      } else {
-        int i = gx - 2 * g.lo[0], j = gy - 2 * g.lo[1];
-        i = i < 0 ? 0 : (i >= g.m[0] ? g.m[0] - 1 : i);
-        j = j < 0 ? 0 : (j >= g.m[1] ? g.m[1] - 1 : j);
-        src = (f == 3 ? g.lam : g.mu) + ((int64_t)kc * g.m[1] + j) * g.m[0] + i;
-      }
-    }
-    cp_async4(dst + idx, src, ok ? 4 : 0);
+  for (int idx = threadIdx.y * kTP + threadIdx.x; idx < kNF * kTYS * kCPR; idx += kTP * kTY) {
+    const int f = idx / (kTYS * kCPR), r = (idx / kCPR) % kTYS, ch = idx % kCPR;
+    const int gx = xs + 4 * ch, gy = y0 - 2 + r;
+    const bool ok = kin && gx >= 0 && gx < g.px && gy >= 0 && gy < g.n[1];
+    const float *src = ok ? a.Y + (int64_t)(9 + f) * S + ((int64_t)K * g.n[1] + gy) * g.px + gx : a.Y;
+    cp_async16(dst + f * kFS + r * kTXS + 4 * ch, src, ok ? 16 : 0);
   }
 }
 
@@ -267,6 +259,8 @@ __device__ __forceinline__ void load_plane(const Geo &g, const StageArgs &a, flo
 __global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g, StageArgs a) {
   float *smem = s_ring;
   const int x0 = g.box_lo[0] - 1 + 2 * kTP * blockIdx.x;  // even: pairs (even, odd)
+  const int xs = (x0 - 2) & ~3;                            // first x of the smem rows
+  const int sh = x0 - 2 - xs;                              // 0 or 2
   const int y0 = g.box_lo[1] + kTY * blockIdx.y;
   const int k0 = g.box_lo[2] + kKC * blockIdx.z;
   const int k1 = min(k0 + kKC - 1, g.box_hi[2]);
@@ -276,19 +270,19 @@ __global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g,
   const bool odd_ok = rowok && IO >= g.box_lo[0] && IO <= g.box_hi[0];
   const int sy = (J & 1) ? kOdd : kEven;
   const float sc = -(g.inv_h * g.inv_h * (1.f / 3.f)) / g.rho;
-  for (int K = k0 - 2; K <= k0 + 2; K++) load_plane(g, a, smem + ((K + 12) % kRing) * kPS, K, x0, y0);
+  for (int K = k0 - 2; K <= k0 + 2; K++) load_plane(g, a, smem + ((K + 12) % kRing) * kPS, K, xs, y0);
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
   for (int K = k0; K <= k1; K++) {
     // plane K+3 streams into the free ring slot while plane K is computed
-    if (K + 1 <= k1) load_plane(g, a, smem + ((K + 3 + 12) % kRing) * kPS, K + 3, x0, y0);
+    if (K + 1 <= k1) load_plane(g, a, smem + ((K + 3 + 12) % kRing) * kPS, K + 3, xs, y0);
     cp_async_commit();
     Tile t;
 #pragma unroll
     for (int d = 0; d < 5; d++) t.pl[d] = ((K + d - 2 + 12) % kRing) * kPS;
     const int sz = (K & 1) ? kOdd : ((K == 0 && !g.top_dir) ? kTop : kEven);
-    t.o = (threadIdx.y + 2) * kTXS + 2 + 2 * threadIdx.x;
+    t.o = (threadIdx.y + 2) * kTXS + 2 + sh + 2 * threadIdx.x;
     t.lam = g.lam;
     t.mu = g.mu;
     t.ms1 = g.m[0];
