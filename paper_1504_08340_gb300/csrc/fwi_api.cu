@@ -35,6 +35,7 @@ struct fwi_ctx {
   float *d_ialpha[3] = {nullptr, nullptr, nullptr};
   std::vector<double> h_alpha[3], h_beta[3];
   float *d_lam = nullptr, *d_mu = nullptr;
+  float *d_lam_n = nullptr, *d_mu_n = nullptr;  // the material in the state layout (Geo::lam_n)
   int *d_shell = nullptr, *d_face = nullptr;
   bool have_material = false;
 
@@ -555,9 +556,13 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   }
   if (st == FWI_OK) st = dalloc(c, &c->d_lam, (size_t)g.nmat);
   if (st == FWI_OK) st = dalloc(c, &c->d_mu, (size_t)g.nmat);
+  if (st == FWI_OK) st = dalloc(c, &c->d_lam_n, (size_t)g.stride);
+  if (st == FWI_OK) st = dalloc(c, &c->d_mu_n, (size_t)g.stride);
   if (st == FWI_OK) {
     g.lam = c->d_lam;
     g.mu = c->d_mu;
+    g.lam_n = c->d_lam_n;
+    g.mu_n = c->d_mu_n;
     for (int b = 0; b < 4 && st == FWI_OK; b++)
       if (cudaMemset(c->state[b], 0, sizeof(float) * sbytes) != cudaSuccess)
         st = fail(c, FWI_E_CUDA, "state clear failed");
@@ -585,6 +590,8 @@ void fwi_destroy(fwi_ctx *c) {
   }
   dfree(c->d_lam);
   dfree(c->d_mu);
+  dfree(c->d_lam_n);
+  dfree(c->d_mu_n);
   dfree(c->d_shell);
   dfree(c->d_face);
   dfree(c->d_wave);
@@ -663,6 +670,8 @@ fwi_status fwi_set_material(fwi_ctx *c, const float *lambda, const float *mu, in
     return fail(c, FWI_E_UNSTABLE, "dt * vp_max / (h/2) = %.3f above the RK4 limit estimate 0.66", cfl);
   CUDA_TRY(c, cudaMemcpyAsync(c->d_lam, hl.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_mu, hm.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  fwi::launch_extend_material(c->geo, c->d_lam_n, c->d_mu_n, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->have_material = true;
   return FWI_OK;
@@ -962,6 +971,7 @@ fwi_status absmax(fwi_ctx *c, const double *x, double *out) {
 fwi_status set_trial(fwi_ctx *c, double alpha, const double *d, int *ok) {
   CUDA_TRY(c, cudaMemsetAsync(c->d_oflags, 0, 2 * sizeof(unsigned), c->stream));
   fwi::opt_trial(c->d_m, d, alpha, c->d_lam, c->d_mu, c->geo.nmat, c->d_oflags, c->stream);
+  fwi::launch_extend_material(c->geo, c->d_lam_n, c->d_mu_n, c->stream);
   unsigned fl[2] = {0, 0};
   CUDA_TRY(c, cudaMemcpyAsync(fl, c->d_oflags, sizeof fl, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

@@ -28,6 +28,7 @@ struct Geo {
   const float *ialpha[3]; // 1 / alpha_s (rounded from FP64)
   const float *beta[3];   // stretch beta_s, 1/s
   const float *lam, *mu;  // interior material grid [k][j][i]
+  const float *lam_n, *mu_n;  // lambda, mu at every node in the state layout (PML: clamped interface value)
   const int *shell;       // node numbers of the interface shell (see shell_kernel)
   int nshell;
   const int *face;        // node numbers of the PML nodes on the grid's outer faces
@@ -98,6 +99,8 @@ void launch_sum(const double *part, int nblocks, double *out, cudaStream_t s);
 
 // flag = 1 if any value of x (n doubles) is not finite.
 void launch_check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);
+// g.lam_n / g.mu_n from the material grid (run whenever lam or mu change)
+void launch_extend_material(const Geo &g, float *lam_n, float *mu_n, cudaStream_t s);
 
 // reduced-space update helpers (fwi_opt.cu); vectors hold (lambda, mu) halves of nmat values
 void opt_wdot(const double *a, const double *b, const double *w, int64_t nmat, double *part, double *out,

@@ -224,6 +224,36 @@ void launch_sum(const double *part, int nblocks, double *out, cudaStream_t s) {
   sum_kernel<<<1, kRedThreads, 0, s>>>(part, nblocks, out);
 }
 
+// lambda, mu at node (i, j, k) of the state layout: the material-grid value, with the
+// coordinates clamped to the interior box for PML nodes (the material extended into
+// the PML); the row padding gets zero
+__global__ void extend_material_kernel(Geo g, float *lam_n, float *mu_n) {
+  const int64_t n = (int64_t)g.px * g.n[1] * g.n[2];
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(idx % g.px);
+    const int64_t r = idx / g.px;
+    const int J = (int)(r % g.n[1]), K = (int)(r / g.n[1]);
+    if (I >= g.n[0]) {
+      lam_n[idx] = 0.f;
+      mu_n[idx] = 0.f;
+      continue;
+    }
+    int i = I - 2 * g.lo[0], j = J - 2 * g.lo[1], k = K - 2 * g.lo[2];
+    i = i < 0 ? 0 : (i >= g.m[0] ? g.m[0] - 1 : i);
+    j = j < 0 ? 0 : (j >= g.m[1] ? g.m[1] - 1 : j);
+    k = k < 0 ? 0 : (k >= g.m[2] ? g.m[2] - 1 : k);
+    const int64_t mi = ((int64_t)k * g.m[1] + j) * g.m[0] + i;
+    lam_n[idx] = g.lam[mi];
+    mu_n[idx] = g.mu[mi];
+  }
+}
+
+void launch_extend_material(const Geo &g, float *lam_n, float *mu_n, cudaStream_t s) {
+  const int64_t n = (int64_t)g.px * g.n[1] * g.n[2];
+  int64_t b = (n + 255) / 256;
+  extend_material_kernel<<<(int)(b > 4096 ? 4096 : b), 256, 0, s>>>(g, lam_n, mu_n);
+}
+
 void launch_check_finite(const double *x, int64_t n, int *flag, cudaStream_t s) {
   finite_kernel<<<misfit_blocks(n), kRedThreads, 0, s>>>(x, n, flag);
 }

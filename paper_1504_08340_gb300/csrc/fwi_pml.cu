@@ -79,13 +79,6 @@ __device__ __forceinline__ float stage_value(const StageArgs &a, int idx, float 
   return (-__ldcs(a.X + idx) + __ldcs(a.Y2 + idx) + 2.f * __ldcs(a.Y3 + idx) + yv) * (1.f / 3.f) + a.cdt * rate;
 }
 
-__device__ __forceinline__ int mat_at(const Geo &g, int I, int J, int K) {
-  int i = I - 2 * g.lo[0], j = J - 2 * g.lo[1], k = K - 2 * g.lo[2];
-  i = i < 0 ? 0 : (i >= g.m[0] ? g.m[0] - 1 : i);
-  j = j < 0 ? 0 : (j >= g.m[1] ? g.m[1] - 1 : j);
-  k = k < 0 ? 0 : (k >= g.m[2] ? g.m[2] - 1 : k);
-  return (k * g.m[1] + j) * g.m[0] + i;
-}
 
 // ---------------------------------------------------------------------------
 // Vectorised pair path: a thread owns the nodes (I0, I0 + 1), I0 even, of a bulk
@@ -194,12 +187,10 @@ __device__ __forceinline__ float2 stage2(const StageArgs &a, int idx, float2 y, 
 // adjoint: column j of sum_lv Lambda^lv_jj tau(T^lv) at the nodes (I0, J, K) and
 // (I0 + 1, J, K), whose Lambda_jj are Lj (levels 0..2), T read at offset o from the pair
 template <int JAX>
-__device__ __forceinline__ void tau_col2(const Geo &g, const float *__restrict__ Y, int S, int o, int I0, int J, int K,
+__device__ __forceinline__ void tau_col2(const Geo &g, const float *__restrict__ Y, int S, int o, int node,
                                          const float2 Lj[3], float2 q[3]) {
   constexpr int KAX = (JAX + 1) % 3, LAX = (JAX + 2) % 3;
-  const int me = mat_at(g, I0, J, K), mo = mat_at(g, I0 + 1, J, K);
-  const float2 lq = make_float2(__ldg(g.lam + me), __ldg(g.lam + mo));
-  const float2 muq = make_float2(__ldg(g.mu + me), __ldg(g.mu + mo));
+  const float2 lq = ld2(g.lam_n + node + o), muq = ld2(g.mu_n + node + o);
   const float2 mu2 = padd(muq, muq);
   q[0] = q[1] = q[2] = bc(0.f);
 #pragma unroll
@@ -216,14 +207,14 @@ __device__ __forceinline__ void tau_col2(const Geo &g, const float *__restrict__
 // adjoint: y- and z-line contributions sum_j D_j Q_cj of a pair, as weighted sums over
 // the line points (C: q[+1] - q[-1]; LR: 0.5 (q[-2] - 4 q[-1] + 4 q[+1] - q[+2]))
 template <int KY, int KZ>
-__device__ __forceinline__ void adj_yz(const Geo &g, const float *__restrict__ Yn, int S, int sy, int sz, int I0, int J,
-                                       int K, const Coef2 &cf, float2 f[3]) {
+__device__ __forceinline__ void adj_yz(const Geo &g, const float *__restrict__ Yn, int S, int sy, int sz, int node,
+                                       const Coef2 &cf, float2 f[3]) {
 #pragma unroll 1
   for (int d = -2; d <= 2; d++) {
     if (d == 0 || (KY == kSC && (d == -2 || d == 2))) continue;
     const float2 w = bc(KY == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f))));
     float2 q[3];
-    tau_col2<1>(g, Yn, S, d * sy, I0, J + d, K, cf.Ly, q);  // (yy, zy, xy) column
+    tau_col2<1>(g, Yn, S, d * sy, node, cf.Ly, q);  // (yy, zy, xy) column
     f[1] = pfma(w, q[0], f[1]); f[2] = pfma(w, q[1], f[2]); f[0] = pfma(w, q[2], f[0]);
   }
 #pragma unroll 1
@@ -231,7 +222,7 @@ __device__ __forceinline__ void adj_yz(const Geo &g, const float *__restrict__ Y
     if (d == 0 || (KZ == kSC && (d == -2 || d == 2))) continue;
     const float2 w = bc(KZ == kSC ? (float)d : (d == -2 ? 0.5f : (d == -1 ? -2.f : (d == 1 ? 2.f : -0.5f))));
     float2 q[3];
-    tau_col2<2>(g, Yn, S, d * sz, I0, J, K + d, cf.Lz, q);  // (zz, xz, yz) column
+    tau_col2<2>(g, Yn, S, d * sz, node, cf.Lz, q);  // (zz, xz, yz) column
     f[2] = pfma(w, q[0], f[2]); f[0] = pfma(w, q[1], f[0]); f[1] = pfma(w, q[2], f[1]);
   }
 }
@@ -254,9 +245,9 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
     {
       const float2 Lx[3] = {bc(cf.Lx[0]), bc(cf.Lx[1]), bc(cf.Lx[2])};
       float2 qm[3], q0[3], qp[3];  // pairs (I0-2, I0-1), (I0, I0+1), (I0+2, I0+3)
-      tau_col2<0>(g, Yn, S, -2, I0 - 2, J, K, Lx, qm);
-      tau_col2<0>(g, Yn, S, 0, I0, J, K, Lx, q0);
-      tau_col2<0>(g, Yn, S, 2, I0 + 2, J, K, Lx, qp);
+      tau_col2<0>(g, Yn, S, -2, node, Lx, qm);
+      tau_col2<0>(g, Yn, S, 0, node, Lx, q0);
+      tau_col2<0>(g, Yn, S, 2, node, Lx, qp);
 #pragma unroll
       for (int c = 0; c < 3; c++) {  // q[0], q[1], q[2]: the xx, yx, zx entries -> components x, y, z
         const float e = 0.5f * (qm[c].x - qp[c].x) + 2.f * (q0[c].y - qm[c].y);
@@ -264,7 +255,7 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
         f[c] = padd(f[c], make_float2(e, o));
       }
     }
-    adj_yz<KY, KZ>(g, Yn, S, sy, sz, I0, J, K, cf, f);
+    adj_yz<KY, KZ>(g, Yn, S, sy, sz, node, cf, f);
   }
   // ---- S rows: H_ij = sum_lv Lambda^lv_jj D_j u^lv_i (times h)
   float2 s[6];
@@ -289,9 +280,7 @@ __device__ void pml_pair(const Geo &g, const StageArgs &a, int I0, int J, int K,
     s[3] = padd(H[1][2], H[2][1]); s[4] = padd(H[0][2], H[2][0]); s[5] = padd(H[0][1], H[1][0]);
   }
   if constexpr (!ADJ && DO_S) {  // tau(P(H)) with the node's own material
-    const int me = mat_at(g, I0, J, K), mo = mat_at(g, I0 + 1, J, K);
-    const float2 lm = make_float2(__ldg(g.lam + me), __ldg(g.lam + mo));
-    const float2 mu = make_float2(__ldg(g.mu + me), __ldg(g.mu + mo));
+    const float2 lm = ld2(g.lam_n + node), mu = ld2(g.mu_n + node);
     const float2 mu2 = padd(mu, mu);
     const float2 ltr = pmul(lm, padd(padd(s[0], s[1]), s[2]));
 #pragma unroll
@@ -430,10 +419,7 @@ __device__ __forceinline__ void face_axis(const Geo &g, const StageArgs &a, cons
           vl += Lv[lv] * __ldg(b + sym(LA, JA) * S + o);
         }
       } else {
-        int cq[3] = {I, J, K};
-        cq[JA] += off;
-        const int mq = mat_at(g, cq[0], cq[1], cq[2]);
-        const float lq = __ldg(g.lam + mq), muq = __ldg(g.mu + mq);
+        const float lq = __ldg(g.lam_n + o), muq = __ldg(g.mu_n + o);
 #pragma unroll
         for (int lv = 0; lv < 3; lv++) {
           const float *b = Y + (9 * lv + 3) * S;
@@ -489,9 +475,8 @@ __device__ __forceinline__ void face_write(const Geo &g, const StageArgs &a, con
   // ---- stress components w and w + 3: S'' = (tau(P(H)) / h - b S' - c S - d Sbar) / a
   float lam = 0.f, mu = 0.f;
   if (!ADJ) {
-    const int mi = mat_at(g, I, J, K);
-    lam = __ldg(g.lam + mi);
-    mu = __ldg(g.mu + mi);
+    lam = __ldg(g.lam_n + n.node);
+    mu = __ldg(g.mu_n + n.node);
   }
 #pragma unroll
   for (int h = 0; h < 2; h++) {

@@ -103,13 +103,6 @@ __device__ __forceinline__ int point_type(int p) { return p == 0 ? kR : (p == 1 
 // symmetric component index: xx yy zz yz xz xy
 __host__ __device__ constexpr int sym(int i, int j) { return i == j ? i : (i + j == 1 ? 5 : (i + j == 2 ? 4 : 3)); }
 
-__device__ __forceinline__ int64_t mat_index(const Geo &g, int I, int J, int K) {
-  int i = I - 2 * g.lo[0], j = J - 2 * g.lo[1], k = K - 2 * g.lo[2];
-  i = i < 0 ? 0 : (i > g.m[0] - 1 ? g.m[0] - 1 : i);
-  j = j < 0 ? 0 : (j > g.m[1] - 1 ? g.m[1] - 1 : j);
-  k = k < 0 ? 0 : (k > g.m[2] - 1 ? g.m[2] - 1 : k);
-  return ((int64_t)k * g.m[1] + j) * g.m[0] + i;
-}
 
 // RK4 stage update of one field value with stage-input value yv (see StageArgs;
 // in stage 1 X is the stage input)
@@ -146,8 +139,7 @@ __device__ __forceinline__ void interior_line_point(const Geo &g, const float *_
   const float Sk_j = dsum(U + j * S, q, st[k], ax[k], all_sides);
   const float Sl_l = dsum(U + l * S, q, st[l], ax[l], all_sides);
   const float Sl_j = dsum(U + j * S, q, st[l], ax[l], all_sides);
-  const int64_t mi = mat_index(g, cq[0], cq[1], cq[2]);
-  const float lam = __ldg(g.lam + mi), mu = __ldg(g.mu + mi);
+  const float lam = __ldg(g.lam_n + q), mu = __ldg(g.mu_n + q);
   const float n2 = nk * nl;
   sj_ = lam * (n2 * dj_j + nl * Sk_k + nk * Sl_l) + 2.f * mu * n2 * dj_j;
   sk_ = mu * (n2 * dj_k + nl * Sk_j);
@@ -227,10 +219,7 @@ __device__ __forceinline__ void pml_force_axis(const Geo &g, const float *__rest
           vl += Lv[lv] * __ldg(b + sym(l, j) * S + q);
         }
       } else {
-        int cq[3] = {c3[0], c3[1], c3[2]};
-        cq[j] += off;
-        const int64_t mi = mat_index(g, cq[0], cq[1], cq[2]);
-        const float lam = __ldg(g.lam + mi), mu = __ldg(g.mu + mi);
+        const float lam = __ldg(g.lam_n + q), mu = __ldg(g.mu_n + q);
 #pragma unroll
         for (int lv = 0; lv < 3; lv++) {
           const float *b = Y + (int64_t)(9 * lv + 3) * S;
@@ -382,8 +371,7 @@ __device__ __forceinline__ void shell_stress(const Geo &g, const StageArgs &a, c
   };
   float src = P(c);
   if (!ADJ) {  // tau(P(H)) = mu (P + diag P) + lambda tr(P) I
-    const int64_t mi = mat_index(g, n.c3[0], n.c3[1], n.c3[2]);
-    const float lam = __ldg(g.lam + mi), mu = __ldg(g.mu + mi);
+    const float lam = __ldg(g.lam_n + n.node), mu = __ldg(g.mu_n + n.node);
     src = c < 3 ? 2.f * mu * src + lam * (P(0) + P(1) + P(2)) : mu * src;
   }
   const float s0 = __ldg(Y + i0), s1 = __ldg(Y + i1), s2 = __ldg(Y + i2);
