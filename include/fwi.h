@@ -229,6 +229,18 @@ fwi_status fwi_regularization(fwi_ctx *ctx, int kind, double eps, double *R, dou
  * allocated by the next gradient call. Errors: FWI_E_INVAL (null context). */
 fwi_status fwi_set_checkpointing(fwi_ctx *ctx, int interval);
 
+/* Number of shots B that one launch of each stage kernel advances together
+ * (default 1). The shots of a fwi_forward, fwi_misfit, fwi_adjoint_gradient or
+ * fwi_step call (each shot an independent wave problem on the same material,
+ * Sec. 3: the misfit and the gradient are sums over the shots) run in groups of
+ * B: the RK4 state sets, traces, residuals, observed-trace slots, displacement
+ * history and snapshots hold B shots each, shot b of a group at b times one
+ * shot's size. Results are those of B = 1: traces bitwise, J and the gradients
+ * up to the order of the FP64 sums over the shots. Device memory grows about B
+ * times. Reallocates those buffers (synchronising the context's stream) when B
+ * changes. Errors: FWI_E_INVAL (B outside [1, 1024]), FWI_E_NOMEM. */
+fwi_status fwi_set_shot_batch(fwi_ctx *ctx, int batch);
+
 /* Current material ([k][j][i] as in fwi_set_material; host or device). */
 fwi_status fwi_get_material(fwi_ctx *ctx, float *lambda, float *mu, int on_device);
 

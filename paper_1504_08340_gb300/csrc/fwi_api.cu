@@ -29,7 +29,8 @@ struct fwi_ctx {
   std::string err;
   int64_t nelem = 0, npml_nodes = 0;
 
-  float *state[4] = {nullptr, nullptr, nullptr, nullptr};  // X, Y2, Y3, Y4
+  float *state[4] = {nullptr, nullptr, nullptr, nullptr};  // X, Y2, Y3, Y4; each [batch][27][stride]
+  int batch = 1;  // shots advanced together by one launch of each stage kernel (fwi_set_shot_batch)
   float *d_alpha[3] = {nullptr, nullptr, nullptr};
   float *d_beta[3] = {nullptr, nullptr, nullptr};
   float *d_ialpha[3] = {nullptr, nullptr, nullptr};
@@ -132,6 +133,11 @@ void dfree(T *&p) {
   if (p) cudaFree((void *)p);
   p = nullptr;
 }
+
+// floats of one shot's RK4 state set, of one shot's traces (or residuals), of one history level
+size_t set_floats(const fwi_ctx *c) { return (size_t)fwi::kFields * c->geo.stride; }
+size_t trace_floats(const fwi_ctx *c) { return (size_t)(c->cfg.nsteps + 1) * c->nrec * 3; }
+size_t level_floats(const fwi_ctx *c) { return (size_t)3 * c->geo.nmat; }
 
 bool is_dirichlet(const fwi_ctx *c, int i, int j, int k) {
   const int *n = c->geo.n;
@@ -237,14 +243,16 @@ fwi_status point(fwi_ctx *c, const fwi::PointArgs &p) {
 }
 
 fwi_status zero_state(fwi_ctx *c) {
-  const size_t bytes = sizeof(float) * (size_t)fwi::kFields * c->geo.stride;
+  const size_t bytes = sizeof(float) * set_floats(c) * c->batch;
   for (int b = 0; b < 4; b++) CUDA_TRY(c, cudaMemsetAsync(c->state[b], 0, bytes, c->stream));
   return FWI_OK;
 }
 
 // One RK4 step (4 fused stage kernels) of the forward (adj = false) or the
 // reversed-time adjoint (adj = true) system, with the point loads of the step.
-fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot, float *hist_slot) {
+// nb shots (shot0 .. shot0 + nb - 1 for the sources) advance together; shot b's history
+// level goes to hist_slot + b * hstride
+fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot0, int nb, float *hist_slot, int64_t hstride) {
   const float dt = (float)c->cfg.dt;
   float *X = c->state[0], *Y2 = c->state[1], *Y3 = c->state[2], *Y4 = c->state[3];
   const float *ins[4] = {X, Y2, Y3, Y4};
@@ -261,17 +269,23 @@ fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot, float *hist_slot) {
     a.cdt = cdt[s];
     a.stage = s + 1;
     a.hist = (s == 3) ? hist_slot : nullptr;
+    a.nshot = nb;
+    a.sstride = (int64_t)set_floats(c);
+    a.hstride = hstride;
     TRY(stage(c, adj, a));
     fwi::PointArgs p{};
     p.buf = outs[s];
     p.stride = c->geo.stride;
     p.cdt = cdt[s];
+    p.nshot = nb;
+    p.sstride = (int64_t)set_floats(c);
+    p.tstride = (int64_t)trace_floats(c);
     if (!adj) {
       // stage times t_n, t_n + dt/2, t_n + dt/2, t_n + dt; wavelet sampled every dt/2
       p.mode = 0;
       p.npts = 1;
-      p.node = c->d_src_node + shot;
-      p.vec = c->d_src_vec + 3 * shot;
+      p.node = c->d_src_node + shot0;
+      p.vec = c->d_src_vec + 3 * shot0;
       p.table = c->d_wave;
       p.i0 = (s == 0) ? 2 * n : (s == 3 ? 2 * n + 2 : 2 * n + 1);
       p.i1 = -1;
@@ -301,7 +315,7 @@ fwi_status require_ready(fwi_ctx *c, int shot0, int nshots) {
 }
 
 fwi_status ensure_trace_buffers(fwi_ctx *c) {
-  const size_t nt = (size_t)(c->cfg.nsteps + 1) * c->nrec * 3;
+  const size_t nt = trace_floats(c) * c->batch;
   TRY(dalloc(c, &c->d_traces, nt));
   TRY(dalloc(c, &c->d_obs, nt));
   TRY(dalloc(c, &c->d_resid, nt));
@@ -310,22 +324,29 @@ fwi_status ensure_trace_buffers(fwi_ctx *c) {
   return FWI_OK;
 }
 
-// forward sweep of one shot into d_traces; hist: optional displacement history;
-// snap: optional snapshots of the step-start state X every `every` steps
-fwi_status forward_sweep(fwi_ctx *c, int shot, float *hist, float *snap = nullptr, int every = 0) {
+// forward sweep of shots shot0 .. shot0 + nb - 1 into d_traces (shot b at b * trace_floats);
+// hist: optional displacement history (shot b at b * hstride); snap: optional snapshots of
+// the step-start state X every `every` steps (shot b's segment g at (b * nseg + g) * set)
+fwi_status forward_sweep(fwi_ctx *c, int shot0, int nb, float *hist, int64_t hstride, float *snap = nullptr,
+                         int every = 0, int nseg = 0) {
   TRY(zero_state(c));
   const int64_t per_step = (int64_t)c->nrec * 3;
-  const size_t hstep = (size_t)3 * c->geo.nmat;
-  const size_t sfloats = (size_t)fwi::kFields * c->geo.stride;
-  if (hist) CUDA_TRY(c, cudaMemsetAsync(hist, 0, sizeof(float) * hstep, c->stream));
-  fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces, c->stream);
+  const size_t hstep = level_floats(c);
+  const size_t sfloats = set_floats(c);
+  const int64_t tf = (int64_t)trace_floats(c);
+  if (hist)
+    for (int b = 0; b < nb; b++)
+      CUDA_TRY(c, cudaMemsetAsync(hist + b * hstride, 0, sizeof(float) * hstep, c->stream));
+  fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces, c->stream, nb,
+                     (int64_t)sfloats, tf);
   for (int n = 0; n < c->cfg.nsteps; n++) {
     if (snap && n % every == 0)
-      CUDA_TRY(c, cudaMemcpyAsync(snap + (size_t)(n / every) * sfloats, c->state[0], sfloats * sizeof(float),
-                                  cudaMemcpyDeviceToDevice, c->stream));
-    TRY(rk4_step(c, false, n, shot, hist ? hist + (size_t)(n + 1) * hstep : nullptr));
+      for (int b = 0; b < nb; b++)
+        CUDA_TRY(c, cudaMemcpyAsync(snap + ((size_t)b * nseg + n / every) * sfloats, c->state[0] + b * sfloats,
+                                    sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    TRY(rk4_step(c, false, n, shot0, nb, hist ? hist + (size_t)(n + 1) * hstep : nullptr, hstride));
     fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces + (n + 1) * per_step,
-                       c->stream);
+                       c->stream, nb, (int64_t)sfloats, tf);
     c->t_launch[2]++;
     c->t_launch[3]++;
   }
@@ -333,12 +354,12 @@ fwi_status forward_sweep(fwi_ctx *c, int shot, float *hist, float *snap = nullpt
   return FWI_OK;
 }
 
-// residual and misfit of the traces in d_traces against observed (device) -> d_J[slot]
-fwi_status misfit_of_traces(fwi_ctx *c, const float *obs_dev, int slot) {
+// residual and misfit of the traces of batch shot b against observed (device) -> d_J[slot]
+fwi_status misfit_of_traces(fwi_ctx *c, int b, const float *obs_dev, int slot) {
   const int64_t per_step = (int64_t)c->nrec * 3;
   const int64_t n = per_step * (c->cfg.nsteps + 1);
-  fwi::launch_residual(c->d_traces, obs_dev, c->d_resid, n, per_step, c->cfg.nsteps, c->cfg.dt, c->d_part,
-                       c->d_flag, c->stream);
+  fwi::launch_residual(c->d_traces + b * n, obs_dev, c->d_resid + b * n, n, per_step, c->cfg.nsteps, c->cfg.dt,
+                       c->d_part, c->d_flag, c->stream);
   fwi::launch_sum(c->d_part, fwi::misfit_blocks(n), c->d_J + slot, c->stream);
   c->t_launch[3] += 2;
   CUDA_TRY(c, cudaGetLastError());
@@ -354,17 +375,19 @@ fwi_status ensure_J(fwi_ctx *c, int n) {
   return FWI_OK;
 }
 
-const float *observed_for_shot(fwi_ctx *c, const float *observed, int on_device, int s, fwi_status *st) {
-  const size_t nt = (size_t)(c->cfg.nsteps + 1) * c->nrec * 3;
+// observed traces of shot s (counted from the call's first shot) on the device; host data
+// go through the batch slot b of d_obs
+const float *observed_for_shot(fwi_ctx *c, const float *observed, int on_device, int s, int b, fwi_status *st) {
+  const size_t nt = trace_floats(c);
   *st = FWI_OK;
   if (on_device) return observed + (size_t)s * nt;
-  cudaError_t e = cudaMemcpyAsync(c->d_obs, observed + (size_t)s * nt, nt * sizeof(float), cudaMemcpyHostToDevice,
-                                  c->stream);
+  cudaError_t e = cudaMemcpyAsync(c->d_obs + (size_t)b * nt, observed + (size_t)s * nt, nt * sizeof(float),
+                                  cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) {
     *st = fail(c, FWI_E_CUDA, "observed upload: %s", cudaGetErrorString(e));
     return nullptr;
   }
-  return c->d_obs;
+  return c->d_obs + (size_t)b * nt;
 }
 
 fwi_status finish_J(fwi_ctx *c, int nshots, double *J) {
@@ -772,10 +795,11 @@ fwi_status fwi_forward(fwi_ctx *c, int shot0, int nshots, float *traces, int on_
   if (!traces) return fail(c, FWI_E_INVAL, "null traces");
   TRY(ensure_trace_buffers(c));
   CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-  const size_t nt = (size_t)(c->cfg.nsteps + 1) * c->nrec * 3;
-  for (int s = 0; s < nshots; s++) {
-    TRY(forward_sweep(c, shot0 + s, nullptr));
-    CUDA_TRY(c, cudaMemcpyAsync(traces + s * nt, c->d_traces, nt * sizeof(float),
+  const size_t nt = trace_floats(c);
+  for (int s0 = 0; s0 < nshots; s0 += c->batch) {
+    const int nb = std::min(c->batch, nshots - s0);
+    TRY(forward_sweep(c, shot0 + s0, nb, nullptr, 0));
+    CUDA_TRY(c, cudaMemcpyAsync(traces + s0 * nt, c->d_traces, nb * nt * sizeof(float),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -789,37 +813,42 @@ fwi_status run_misfit(fwi_ctx *c, int shot0, int nshots, const float *observed, 
   TRY(ensure_trace_buffers(c));
   TRY(ensure_J(c, nshots));
   CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-  for (int s = 0; s < nshots; s++) {
-    TRY(forward_sweep(c, shot0 + s, nullptr));
-    fwi_status st;
-    const float *obs = observed_for_shot(c, observed, on_device, s, &st);
-    if (!obs) return st;
-    TRY(misfit_of_traces(c, obs, s));
+  for (int s0 = 0; s0 < nshots; s0 += c->batch) {
+    const int nb = std::min(c->batch, nshots - s0);
+    TRY(forward_sweep(c, shot0 + s0, nb, nullptr, 0));
+    for (int b = 0; b < nb; b++) {
+      fwi_status st;
+      const float *obs = observed_for_shot(c, observed, on_device, s0 + b, b, &st);
+      if (!obs) return st;
+      TRY(misfit_of_traces(c, b, obs, s0 + b));
+    }
   }
   return finish_J(c, nshots, J);
 }
 
 // misfit and g_mis (dJ/dlambda_i, dJ/dmu_i) into d_gl / d_gm
 // (re)allocate the displacement history for `slots` levels
+// history slots (levels) per shot of the batch; shot b's levels start at b * slots levels
 fwi_status ensure_hist(fwi_ctx *c, size_t slots) {
-  if (c->hist_cap >= slots) return FWI_OK;
+  if (c->hist_cap >= slots * c->batch) return FWI_OK;
   dfree(c->d_hist);
   c->hist_cap = 0;
-  TRY(dalloc(c, &c->d_hist, slots * 3 * (size_t)c->geo.nmat));
-  c->hist_cap = slots;
+  TRY(dalloc(c, &c->d_hist, slots * c->batch * level_floats(c)));
+  c->hist_cap = slots * c->batch;
   return FWI_OK;
 }
 
-// the adjoint step that yields w(t_lvl), and the gradient integrand at that level
-// from the displacement history slot `hist_lvl`
-fwi_status adjoint_level(fwi_ctx *c, int lvl, const float *hist_lvl) {
+// the adjoint step that yields w(t_lvl) for the nb shots of the batch, and the gradient
+// integrand at that level from their displacement history slots (shot b at hist_lvl + b hstride)
+fwi_status adjoint_level(fwi_ctx *c, int lvl, const float *hist_lvl, int nb, int64_t hstride) {
   const int N = c->cfg.nsteps;
-  TRY(rk4_step(c, true, N - lvl - 1, 0, nullptr));
+  TRY(rk4_step(c, true, N - lvl - 1, 0, nb, nullptr, 0));
   if (lvl > 0) {
     const double wn = (lvl == N) ? 0.5 : 1.0;
     cudaEvent_t e0;
     time_begin(c, &e0);
-    fwi::launch_gradient(c->geo, c->state[0], hist_lvl, wn * c->cfg.dt, c->d_gl, c->d_gm, c->stream);
+    fwi::launch_gradient(c->geo, c->state[0], hist_lvl, wn * c->cfg.dt, c->d_gl, c->d_gm, c->stream, nb,
+                         (int64_t)set_floats(c), hstride);
     time_end(c, e0, 1);
     CUDA_TRY(c, cudaGetLastError());
   }
@@ -831,25 +860,28 @@ fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed
   TRY(ensure_J(c, nshots));
   const size_t nmat = (size_t)c->geo.nmat;
   const int N = c->cfg.nsteps;
-  const size_t hstep = 3 * nmat;
+  const size_t hstep = level_floats(c);
   // checkpoint interval: 0 keeps every level of the displacement history
   int every = c->ckpt < 0 ? (int)std::ceil(std::sqrt((double)N)) : c->ckpt;
   if (every >= N) every = 0;
   const int nseg = every > 0 ? (N + every - 1) / every : 0;
-  const size_t sfloats = (size_t)fwi::kFields * c->geo.stride;
-  TRY(ensure_hist(c, every > 0 ? (size_t)every + 1 : (size_t)N + 1));
+  const size_t sfloats = set_floats(c);
+  const size_t slots = every > 0 ? (size_t)every + 1 : (size_t)N + 1;
+  const int64_t hstride = (int64_t)(slots * hstep);  // one shot's history levels
+  TRY(ensure_hist(c, slots));
   if (every > 0) {
-    if (c->snap_cap < (size_t)nseg) {
+    const size_t nsnap = (size_t)nseg * c->batch;
+    if (c->snap_cap < nsnap) {
       dfree(c->d_snap);
       c->snap_cap = 0;
-      TRY(dalloc(c, &c->d_snap, (size_t)nseg * sfloats));
-      c->snap_cap = nseg;
+      TRY(dalloc(c, &c->d_snap, nsnap * sfloats));
+      c->snap_cap = nsnap;
     }
     for (int b = 0; b < 4; b++) {
       if (c->rstate[b]) continue;
-      TRY(dalloc(c, &c->rstate[b], sfloats));
+      TRY(dalloc(c, &c->rstate[b], sfloats * c->batch));
       // entries that no stage writes (history and stress off the PML, fixed faces, padding) stay zero
-      CUDA_TRY(c, cudaMemsetAsync(c->rstate[b], 0, sfloats * sizeof(float), c->stream));
+      CUDA_TRY(c, cudaMemsetAsync(c->rstate[b], 0, sfloats * c->batch * sizeof(float), c->stream));
     }
   }
   TRY(dalloc(c, &c->d_gl, nmat));
@@ -857,17 +889,20 @@ fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed
   CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_gl, 0, sizeof(double) * nmat, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_gm, 0, sizeof(double) * nmat, c->stream));
-  for (int s = 0; s < nshots; s++) {
-    const int shot = shot0 + s;
-    TRY(forward_sweep(c, shot, every > 0 ? nullptr : c->d_hist, every > 0 ? c->d_snap : nullptr, every));
-    fwi_status st;
-    const float *obs = observed_for_shot(c, observed, on_device, s, &st);
-    if (!obs) return st;
-    TRY(misfit_of_traces(c, obs, s));
+  for (int s0 = 0; s0 < nshots; s0 += c->batch) {
+    const int nb = std::min(c->batch, nshots - s0);
+    TRY(forward_sweep(c, shot0 + s0, nb, every > 0 ? nullptr : c->d_hist, hstride, every > 0 ? c->d_snap : nullptr,
+                      every, nseg));
+    for (int b = 0; b < nb; b++) {
+      fwi_status st;
+      const float *obs = observed_for_shot(c, observed, on_device, s0 + b, b, &st);
+      if (!obs) return st;
+      TRY(misfit_of_traces(c, b, obs, s0 + b));
+    }
     // adjoint sweep in reversed time with the gradient time integral (C.1f)/(C.1g)
     TRY(zero_state(c));
     if (every == 0) {
-      for (int lvl = N - 1; lvl >= 0; lvl--) TRY(adjoint_level(c, lvl, c->d_hist + (size_t)lvl * hstep));
+      for (int lvl = N - 1; lvl >= 0; lvl--) TRY(adjoint_level(c, lvl, c->d_hist + (size_t)lvl * hstep, nb, hstride));
       continue;
     }
     // checkpointed: segment g holds the steps [g every, min((g+1) every, N)). Its forward
@@ -879,15 +914,16 @@ fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed
       const int L0 = g * every, L1 = std::min(L0 + every, N);
       std::swap(c->state, c->rstate);
       fwi_status rs = FWI_OK;
-      if (cudaMemcpyAsync(c->state[0], c->d_snap + (size_t)g * sfloats, sfloats * sizeof(float),
-                          cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-        rs = fail(c, FWI_E_CUDA, "snapshot restore failed");
+      for (int b = 0; b < nb && rs == FWI_OK; b++)
+        if (cudaMemcpyAsync(c->state[0] + b * sfloats, c->d_snap + ((size_t)b * nseg + g) * sfloats,
+                            sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+          rs = fail(c, FWI_E_CUDA, "snapshot restore failed");
       for (int n = L0; n < L1 && rs == FWI_OK; n++)
-        rs = rk4_step(c, false, n, shot, c->d_hist + (size_t)(n + 1 - L0) * hstep);
+        rs = rk4_step(c, false, n, shot0 + s0, nb, c->d_hist + (size_t)(n + 1 - L0) * hstep, hstride);
       std::swap(c->state, c->rstate);
       TRY(rs);
       for (int lvl = std::min(L1, N - 1); lvl > L0; lvl--)
-        TRY(adjoint_level(c, lvl, c->d_hist + (size_t)(lvl - L0) * hstep));
+        TRY(adjoint_level(c, lvl, c->d_hist + (size_t)(lvl - L0) * hstep, nb, hstride));
     }
   }
   fwi::launch_check_finite(c->d_gl, (int64_t)nmat, c->d_flag, c->stream);
@@ -1220,6 +1256,7 @@ fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int
   a.X = in;
   a.out = out;
   a.stage = 0;
+  a.nshot = 1;
   TRY(stage(c, adjoint != 0, a));
   if (!on_device)
     CUDA_TRY(c, cudaMemcpyAsync(rate, c->state[2], n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -1255,6 +1292,29 @@ fwi_status fwi_regularization(fwi_ctx *c, int kind, double eps, double *R, doubl
       CUDA_TRY(c, cudaMemcpyAsync(out[p], g, nmat * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
   CUDA_TRY(c, cudaMemcpyAsync(R, c->d_rval, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
+fwi_status fwi_set_shot_batch(fwi_ctx *c, int batch) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (batch < 1 || batch > 1024) return fail(c, FWI_E_INVAL, "shot batch %d outside [1, 1024]", batch);
+  if (batch == c->batch) return FWI_OK;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // every per-shot buffer is sized by the batch: drop them all, then the state sets again
+  for (int b = 0; b < 4; b++) {
+    dfree(c->state[b]);
+    dfree(c->rstate[b]);
+  }
+  for (float **p : {&c->d_snap, &c->d_hist, &c->d_traces, &c->d_obs, &c->d_resid}) dfree(*p);
+  c->snap_cap = c->hist_cap = 0;
+  c->batch = batch;
+  const size_t n = set_floats(c) * batch;
+  for (int b = 0; b < 4; b++) {
+    TRY(dalloc(c, &c->state[b], n));
+    CUDA_TRY(c, cudaMemsetAsync(c->state[b], 0, n * sizeof(float), c->stream));
+  }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return FWI_OK;
 }

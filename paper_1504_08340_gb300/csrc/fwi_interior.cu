@@ -256,13 +256,16 @@ __device__ __forceinline__ void load_plane(const Geo &g, const StageArgs &a, flo
 #ifndef FWI_INT_MINB
 #define FWI_INT_MINB 2
 #endif
-__global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g, StageArgs a) {
+__global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g, StageArgs a0) {
   float *smem = s_ring;
+  const int nzc = (g.box_hi[2] - g.box_lo[2] + kKC) / kKC;  // z chunks per shot
+  const StageArgs a = shot_args(a0, blockIdx.z / nzc);
+  const int bz = blockIdx.z % nzc;
   const int x0 = g.box_lo[0] - 1 + 2 * kTP * blockIdx.x;  // even: pairs (even, odd)
   const int xs = (x0 - 2) & ~3;                            // first x of the smem rows
   const int sh = x0 - 2 - xs;                              // 0 or 2
   const int y0 = g.box_lo[1] + kTY * blockIdx.y;
-  const int k0 = g.box_lo[2] + kKC * blockIdx.z;
+  const int k0 = g.box_lo[2] + kKC * bz;
   const int k1 = min(k0 + kKC - 1, g.box_hi[2]);
   const int IE = x0 + 2 * threadIdx.x, IO = IE + 1, J = y0 + threadIdx.y;
   const bool rowok = J <= g.box_hi[1];
@@ -319,7 +322,7 @@ int launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s) {
   if (g.box_hi[0] < g.box_lo[0] || g.box_hi[1] < g.box_lo[1] || g.box_hi[2] < g.box_lo[2]) return 0;
   const int nx = g.box_hi[0] - (g.box_lo[0] - 1) + 1;
   const dim3 grd((nx + 2 * kTP - 1) / (2 * kTP), (g.box_hi[1] - g.box_lo[1] + kTY) / kTY,
-                 (g.box_hi[2] - g.box_lo[2] + kKC) / kKC);
+                 (g.box_hi[2] - g.box_lo[2] + kKC) / kKC * a.nshot);
   interior_kernel<<<grd, dim3(kTP, kTY), kSmem, s>>>(g, a);
   return 1;
 }

@@ -47,7 +47,23 @@ struct StageArgs {
   float cdt;
   int stage;
   float *hist;       // stage 4: interior displacement written here as [3][nmat], or null
+  // a batch of nshot shots: shot b's buffers start sstride floats (history: hstride)
+  // after shot b-1's; one launch of each stage kernel advances every shot of the batch
+  int nshot;
+  int64_t sstride, hstride;
 };
+
+// the buffers of shot `shot` of the batch
+__host__ __device__ inline StageArgs shot_args(StageArgs a, int shot) {
+  const int64_t o = (int64_t)shot * a.sstride;
+  a.Y += o;
+  if (a.X) a.X += o;
+  if (a.Y2) a.Y2 += o;
+  if (a.Y3) a.Y3 += o;
+  a.out += o;
+  if (a.hist) a.hist += (int64_t)shot * a.hstride;
+  return a;
+}
 
 // One RK4 stage is five kernels writing disjoint node sets; they read the same
 // input and may run concurrently on different streams. Each launcher returns the
@@ -78,17 +94,24 @@ struct PointArgs {
   int i0, i1;            // sample indices (i1 < 0: single sample)
   float cdt;
   int mode;
+  // batch: shot b adds into buf + b * sstride; sources: its point is node[b], vec[b];
+  // receivers: its residuals start at table + b * tstride
+  int nshot;
+  int64_t sstride, tstride;
 };
 void launch_point(const PointArgs &p, cudaStream_t s);
 
-// traces[r][c] = buf[9 + c][node[r]]
+// traces[b][r][c] = buf[b * sstride + (9 + c) * stride + node[r]] for the nshot shots of a
+// batch (trace of shot b at traces + b * tstride)
 void launch_sample(const float *buf, int64_t stride, int nrec, const int64_t *node, float *traces,
-                   cudaStream_t s);
+                   cudaStream_t s, int nshot = 1, int64_t sstride = 0, int64_t tstride = 0);
 
 // Gradient integrand of (C.1f)/(C.1g) at one time level, accumulated in FP64:
-// gl[i] -= wdt * sum_e W detJ (div w)(div u), gm[i] -= wdt * sum_e W detJ 2 eps(w):eps(u).
+// gl[i] -= wdt * sum_e W detJ (div w)(div u), gm[i] -= wdt * sum_e W detJ 2 eps(w):eps(u),
+// for the shots b = 0 .. nshot - 1 in order (adjoint state at w_state + b sstride, history
+// level at u_hist + b hstride).
 void launch_gradient(const Geo &g, const float *w_state, const float *u_hist, double wdt, double *gl,
-                     double *gm, cudaStream_t s);
+                     double *gm, cudaStream_t s, int nshot = 1, int64_t sstride = 0, int64_t hstride = 0);
 
 // resid = traces - observed (n values); partial sums of w_n dt e^2 / 2 per block into part;
 // flag set to 1 on a non-finite trace value.

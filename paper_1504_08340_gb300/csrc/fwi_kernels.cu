@@ -57,34 +57,41 @@ __device__ __forceinline__ float dstc(const float *__restrict__ f, int64_t i, in
 }
 
 __global__ void point_kernel(PointArgs p) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.npts) return;
-  const int64_t n = p.node[i];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.npts * p.nshot) return;
+  const int b = t / p.npts, i = t - b * p.npts;  // shot of the batch, point
+  const int k = p.mode == 0 ? b : i;             // sources: one point per shot
+  const int64_t n = p.node[k];
+  float *buf = p.buf + (int64_t)b * p.sstride;
+  const float *table = p.mode == 0 ? p.table : p.table + (int64_t)b * p.tstride;
   for (int c = 0; c < 3; c++) {
     float amp;
     if (p.mode == 0) {
-      amp = p.table[p.i0];
-      if (p.i1 >= 0) amp = 0.5f * (amp + p.table[p.i1]);
+      amp = table[p.i0];
+      if (p.i1 >= 0) amp = 0.5f * (amp + table[p.i1]);
     } else {
-      amp = p.table[((int64_t)p.i0 * p.npts + i) * 3 + c];
-      if (p.i1 >= 0) amp = 0.5f * (amp + p.table[((int64_t)p.i1 * p.npts + i) * 3 + c]);
+      amp = table[((int64_t)p.i0 * p.npts + i) * 3 + c];
+      if (p.i1 >= 0) amp = 0.5f * (amp + table[((int64_t)p.i1 * p.npts + i) * 3 + c]);
     }
-    p.buf[(int64_t)(18 + c) * p.stride + n] += p.cdt * amp * p.vec[i * 3 + c];
+    buf[(int64_t)(18 + c) * p.stride + n] += p.cdt * amp * p.vec[k * 3 + c];
   }
 }
 
-__global__ void sample_kernel(const float *buf, int64_t stride, int nrec, const int64_t *node, float *tr) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nrec * 3) return;
+__global__ void sample_kernel(const float *buf, int64_t stride, int nrec, const int64_t *node, float *tr,
+                              int nshot, int64_t sstride, int64_t tstride) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrec * 3 * nshot) return;
+  const int b = t / (nrec * 3), i = t - b * nrec * 3;
   const int r = i / 3, c = i % 3;
-  tr[i] = buf[(int64_t)(9 + c) * stride + node[r]];
+  tr[(int64_t)b * tstride + i] = buf[(int64_t)b * sstride + (int64_t)(9 + c) * stride + node[r]];
 }
 
 // (C.1f)/(C.1g) at one time level. One thread per interior node; the sum over the
 // interior elements around the node of the element-wise gradients' products.
-__global__ void __launch_bounds__(256) gradient_kernel(Geo g, const float *__restrict__ ws,
-                                                       const float *__restrict__ uh, double wdt,
-                                                       double *gl, double *gm) {
+__global__ void __launch_bounds__(256) gradient_kernel(Geo g, const float *__restrict__ ws0,
+                                                       const float *__restrict__ uh0, double wdt,
+                                                       double *gl, double *gm, int nshot, int64_t sstride,
+                                                       int64_t hstride) {
   const int64_t mi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (mi >= g.nmat) return;
   const int i = (int)(mi % g.m[0]);
@@ -98,6 +105,16 @@ __global__ void __launch_bounds__(256) gradient_kernel(Geo g, const float *__res
   const int64_t sm[3] = {1, (int64_t)g.m[0], (int64_t)g.m[0] * g.m[1]};
   Axis ax[3] = {axis_info(I, g.n[0], g.lo[0], g.hi[0]), axis_info(J, g.n[1], g.lo[1], g.hi[1]),
                 axis_info(K, g.n[2], g.lo[2], g.hi[2])};
+  float W = g.wdetj;
+#pragma unroll
+  for (int x = 0; x < 3; x++) W *= (c3[x] & 1) ? (4.f / 3.f) : (1.f / 3.f);
+  double accl = gl[mi], accm = gm[mi];
+  // the shots of a batch in order: shot b's adjoint state at ws0 + b sstride, its
+  // displacement history level at uh0 + b hstride
+#pragma unroll 1
+  for (int b = 0; b < nshot; b++) {
+  const float *__restrict__ ws = ws0 + b * sstride;
+  const float *__restrict__ uh = uh0 + b * hstride;
   // all loops have fixed trip counts and are unrolled, so the arrays stay in registers
   float dw[3][2][3], du[3][2][3];  // [axis][side][component]
 #pragma unroll
@@ -136,11 +153,11 @@ __global__ void __launch_bounds__(256) gradient_kernel(Geo g, const float *__res
                (Gw[0][1] + Gw[1][0]) * (Gu[1][0] + Gu[0][1]) + (Gw[0][2] + Gw[2][0]) * (Gu[2][0] + Gu[0][2]) +
                (Gw[1][2] + Gw[2][1]) * (Gu[2][1] + Gu[1][2]);
       }
-  float W = g.wdetj;
-#pragma unroll
-  for (int x = 0; x < 3; x++) W *= (c3[x] & 1) ? (4.f / 3.f) : (1.f / 3.f);
-  gl[mi] -= wdt * (double)W * (double)sl;
-  gm[mi] -= wdt * (double)W * (double)smu;
+  accl -= wdt * (double)W * (double)sl;
+  accm -= wdt * (double)W * (double)smu;
+  }
+  gl[mi] = accl;
+  gm[mi] = accm;
 }
 
 constexpr int kRedThreads = 256;
@@ -193,19 +210,21 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 }  // namespace
 
 void launch_point(const PointArgs &p, cudaStream_t s) {
-  if (p.npts <= 0) return;
-  point_kernel<<<blocks_for(p.npts, 128), 128, 0, s>>>(p);
+  if (p.npts <= 0 || p.nshot <= 0) return;
+  point_kernel<<<blocks_for((int64_t)p.npts * p.nshot, 128), 128, 0, s>>>(p);
 }
 
 void launch_sample(const float *buf, int64_t stride, int nrec, const int64_t *node, float *traces,
-                   cudaStream_t s) {
-  if (nrec <= 0) return;
-  sample_kernel<<<blocks_for((int64_t)nrec * 3, 256), 256, 0, s>>>(buf, stride, nrec, node, traces);
+                   cudaStream_t s, int nshot, int64_t sstride, int64_t tstride) {
+  if (nrec <= 0 || nshot <= 0) return;
+  sample_kernel<<<blocks_for((int64_t)nrec * 3 * nshot, 256), 256, 0, s>>>(buf, stride, nrec, node, traces, nshot,
+                                                                           sstride, tstride);
 }
 
 void launch_gradient(const Geo &g, const float *w_state, const float *u_hist, double wdt, double *gl,
-                     double *gm, cudaStream_t s) {
-  gradient_kernel<<<blocks_for(g.nmat, 256), 256, 0, s>>>(g, w_state, u_hist, wdt, gl, gm);
+                     double *gm, cudaStream_t s, int nshot, int64_t sstride, int64_t hstride) {
+  gradient_kernel<<<blocks_for(g.nmat, 256), 256, 0, s>>>(g, w_state, u_hist, wdt, gl, gm, nshot, sstride,
+                                                          hstride);
 }
 
 int misfit_blocks(int64_t n) {

@@ -516,8 +516,10 @@ constexpr int kBX = 32, kBY = FWI_PML_BY;
 // The boxes exclude the outer faces of the grid, so every node takes the bulk path.
 template <bool ADJ, int MODE, int PART>
 __global__ void __launch_bounds__(kBX *kBY, PART == 0 ? FWI_PML_MINB : FWI_PML_SPLIT_MINB)
-    pml_kernel(Geo g, StageArgs a, Region r) {
-  const int task = blockIdx.x * kBY + threadIdx.y;
+    pml_kernel(Geo g, StageArgs a0, Region r) {
+  const int nbs = (r.tasks_before[r.nbox] + kBY - 1) / kBY;  // blocks per shot
+  const StageArgs a = shot_args(a0, blockIdx.x / nbs);
+  const int task = (blockIdx.x % nbs) * kBY + threadIdx.y;
   if (task >= r.tasks_before[r.nbox]) return;
   int b = 0;
   while (b + 1 < r.nbox && task >= r.tasks_before[b + 1]) b++;
@@ -554,10 +556,12 @@ __global__ void __launch_bounds__(kBX *kBY, PART == 0 ? FWI_PML_MINB : FWI_PML_S
 }
 
 template <bool ADJ>
-__global__ void __launch_bounds__(3 * kFaceNodes, FWI_FACE_MINB) pml_face_kernel(Geo g, StageArgs a) {
+__global__ void __launch_bounds__(3 * kFaceNodes, FWI_FACE_MINB) pml_face_kernel(Geo g, StageArgs a0) {
   __shared__ FaceShared sh;
+  const int nbs = (g.nface + kFaceNodes - 1) / kFaceNodes;  // blocks per shot
+  const StageArgs a = shot_args(a0, blockIdx.x / nbs);
   const int lane = threadIdx.x, w = threadIdx.y;
-  const int i = blockIdx.x * kFaceNodes + lane;
+  const int i = (blockIdx.x % nbs) * kFaceNodes + lane;
   const bool live = i < g.nface;
   int I = 0, J = 0, K = 0;
   FaceCtx n;
@@ -623,7 +627,7 @@ int launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
   const Region r = pml_region(g);
   const int tasks = r.tasks_before[r.nbox];
   if (tasks == 0) return 0;
-  const dim3 grd((tasks + kBY - 1) / kBY), blk(kBX, kBY);
+  const dim3 grd((tasks + kBY - 1) / kBY * a.nshot), blk(kBX, kBY);
   const int mode = a.stage == 0 ? 0 : (a.stage == 1 ? 1 : (a.stage < 4 ? 2 : 3));
   auto go = [&](auto part, cudaStream_t st) {
     constexpr int P = decltype(part)::value;
@@ -648,7 +652,7 @@ int launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
 
 int launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
   if (g.nface <= 0) return 0;
-  const int nb = (g.nface + kFaceNodes - 1) / kFaceNodes;
+  const int nb = (g.nface + kFaceNodes - 1) / kFaceNodes * a.nshot;
   const dim3 blk(kFaceNodes, 3);
   if (adjoint)
     pml_face_kernel<true><<<nb, blk, 0, s>>>(g, a);

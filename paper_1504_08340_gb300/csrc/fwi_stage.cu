@@ -409,10 +409,12 @@ __device__ __forceinline__ void shell_disp(const Geo &g, const StageArgs &a, con
 #define FWI_SHELL_MINB 8
 #endif
 template <bool ADJ>
-__global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(Geo g, StageArgs a) {
+__global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(Geo g, StageArgs a0) {
   __shared__ ShellShared sh;
+  const int nbs = (g.nshell + kShellNodes - 1) / kShellNodes;  // blocks per shot
+  const StageArgs a = shot_args(a0, blockIdx.x / nbs);
   const int lane = threadIdx.x, w = threadIdx.y;
-  const int i = blockIdx.x * kShellNodes + lane;
+  const int i = (blockIdx.x % nbs) * kShellNodes + lane;
   const bool live = i < g.nshell;
   NodeCtx n;
   if (live) {
@@ -437,7 +439,7 @@ int launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s)
   int n = 0;
   if (g.nshell > 0) {
     n = 1;
-    const int nb = (g.nshell + kShellNodes - 1) / kShellNodes;
+    const int nb = (g.nshell + kShellNodes - 1) / kShellNodes * a.nshot;
     const dim3 blk(kShellNodes, 3);
     if (adjoint)
       shell_kernel<true><<<nb, blk, 0, s>>>(g, a);

@@ -52,7 +52,8 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
-           "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization")
+           "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization",
+           "fwi_set_shot_batch")
 
 _lib = None
 
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_step_reset.argtypes = [P]
     lib.fwi_get_material.argtypes = [P, P, P, I]
     lib.fwi_set_checkpointing.argtypes = [P, I]
+    lib.fwi_set_shot_batch.argtypes = [P, I]
     lib.fwi_regularization.argtypes = [P, I, C.c_double, D, P, P, I]
     for name in EXPORTS:
         if name not in ("fwi_destroy", "fwi_last_error", "fwi_status_string"):
@@ -287,6 +289,10 @@ class Context:
         pm, _ = _ptr(gm, np.float64)
         self._check(self.lib.fwi_regularization(self.ptr, {"tn": 0, "tv": 1}[kind], float(eps), R, pl, pm, dl))
         return [R[0], R[1]], gl, gm
+
+    def set_shot_batch(self, batch):
+        """Shots advanced together by one launch of each stage kernel (fwi_set_shot_batch)."""
+        self._check(self.lib.fwi_set_shot_batch(self.ptr, int(batch)))
 
     def set_checkpointing(self, interval):
         """0: store u at every step; k > 0: snapshot every k steps and recompute;

@@ -1,0 +1,128 @@
+"""Shot batching: B shots advanced by one launch of each stage kernel.
+
+Each shot is an independent wave problem on the same material (the misfit and the
+gradient of Sec. 3 are sums over the shots), so batching must not change any
+shot's arithmetic: traces are bitwise those of B = 1, J too (the per-shot misfits
+are summed in shot order either way), and the gradients differ only by the order
+of the FP64 sums over the shots. Groups that do not divide the shot count (a
+ragged last group) and B larger than the shot count are covered."""
+import numpy as np
+import pytest
+
+import fwi_inputs as fi
+from helpers import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _workload(nsteps=50):
+    return fi.build(fi.Workload("box_5x4x3", 5, 4, 3, 2, 1.0, nsteps, 30.0, 3, nshots=4, seed=5))
+
+
+def _setup(w):
+    from paper_1504_08340_gb300 import Context
+
+    ctx = Context(w.nx, w.ny, w.nz, w.npml, w.h, w.dt, w.nsteps, rho=w.rho)
+    lt, mt = (_f32(a) for a in fi.medium(w, "true"))
+    l0, m0 = (_f32(a) for a in fi.medium(w, "trial"))
+    ctx.set_sources(w.sources(), w.source_dirs(), "ricker", w.ricker())
+    ctx.set_receivers(w.receivers())
+    ctx.set_material(lt, mt)
+    obs = torch.zeros(ctx.trace_shape(w.nshots), dtype=torch.float32, device="cuda")
+    ctx.forward(0, w.nshots, out=obs)
+    ctx.set_material(l0, m0)
+    return ctx, obs, l0, m0
+
+
+def test_batched_forward_and_misfit_are_bitwise():
+    w = _workload()
+    ctx, obs, _, _ = _setup(w)
+    with ctx:
+        ref = torch.zeros_like(obs)
+        ctx.forward(0, w.nshots, out=ref)
+        J1 = ctx.misfit(obs, 0, w.nshots)
+        Jpart = ctx.misfit(obs[1:3], 1, 2)
+        for B in (2, 3, 4, 7):
+            ctx.set_shot_batch(B)
+            tr = torch.full_like(obs, float("nan"))
+            ctx.forward(0, w.nshots, out=tr)
+            assert torch.equal(tr, ref), B
+            assert ctx.misfit(obs, 0, w.nshots) == J1, B
+            # a shot range that starts inside the shot list
+            assert ctx.misfit(obs[1:3], 1, 2) == Jpart, B
+            # host observed data go through the batch's device slots
+            assert ctx.misfit(obs.cpu().numpy(), 0, w.nshots) == J1, B
+
+
+@pytest.mark.parametrize("every", [0, -1, 9])
+def test_batched_gradient_matches_single_shot_path(every):
+    w = _workload(nsteps=61)
+    ctx, obs, _, _ = _setup(w)
+    with ctx:
+        ctx.set_checkpointing(every)
+        J1, gl1, gm1 = ctx.adjoint_gradient(obs, 0, w.nshots)
+        for B in (3, 4):
+            ctx.set_shot_batch(B)
+            ctx.set_checkpointing(every)
+            J, gl, gm = ctx.adjoint_gradient(obs, 0, w.nshots)
+            assert J == J1, B
+            assert rel_l2(gl.cpu().numpy(), gl1.cpu().numpy()) < 1e-12, B
+            assert rel_l2(gm.cpu().numpy(), gm1.cpu().numpy()) < 1e-12, B
+            ctx.set_shot_batch(1)
+
+
+def test_batched_gradient_matches_oracle(oracle_mod):
+    w = _workload(nsteps=40)
+    ctx, obs, l0, m0 = _setup(w)
+    with ctx:
+        ctx.set_shot_batch(3)
+        J, gl, gm = ctx.adjoint_gradient(obs, 0, w.nshots)
+    o = oracle_mod.Oracle(w.nx, w.ny, w.nz, w.npml, h=w.h, rho=w.rho)
+    src = [o.node_id(*s) for s in w.sources()]
+    rec = [o.node_id(*r) for r in w.receivers()]
+    o.set_material(l0.astype(np.float64), m0.astype(np.float64))
+    ob = obs.cpu().numpy().astype(np.float64)
+    dirs = w.source_dirs()
+    Jo, glo, gmo = 0.0, 0.0, 0.0
+    for s in range(w.nshots):  # the objective and its gradient are sums over the shots
+        Js, gls, gms, _ = o.misfit_and_gradient(w.dt, w.nsteps, [src[s]], dirs[s:s + 1], rec, ob[s], "ricker",
+                                                w.ricker())
+        Jo, glo, gmo = Jo + Js, glo + gls, gmo + gms
+    assert J == pytest.approx(Jo, rel=2e-5)
+    assert rel_l2(gl.cpu().numpy().ravel(), glo.ravel()) < 1e-4
+    assert rel_l2(gm.cpu().numpy().ravel(), gmo.ravel()) < 1e-4
+
+
+def test_batched_step_matches_single_shot_step():
+    w = _workload(nsteps=40)
+    infos = []
+    for B in (1, 4):
+        ctx, obs, _, _ = _setup(w)
+        with ctx:
+            ctx.set_shot_batch(B)
+            infos.append([ctx.step(obs, 0, w.nshots) for _ in range(2)])
+            infos[-1].append(ctx.get_material())
+    (a1, a2, (la, ma)), (b1, b2, (lb, mb)) = infos
+    assert a1.J_old == b1.J_old  # same material, bitwise traces
+    for x, y in ((a1, b1), (a2, b2)):
+        assert x.accepted == y.accepted == 1
+        assert x.J_old == pytest.approx(y.J_old, rel=1e-9)
+        assert x.J_new == pytest.approx(y.J_new, rel=1e-9)
+        assert x.alpha == y.alpha
+    assert rel_l2(lb.ravel().astype(np.float64), la.ravel().astype(np.float64)) < 1e-6
+    assert rel_l2(mb.ravel().astype(np.float64), ma.ravel().astype(np.float64)) < 1e-6
+
+
+def test_shot_batch_rejects_bad_sizes():
+    w = _workload(nsteps=10)
+    ctx, _, _, _ = _setup(w)
+    with ctx:
+        for bad in (0, -1, 1025):
+            with pytest.raises(Exception):
+                ctx.set_shot_batch(bad)
+        ctx.set_shot_batch(1024 // 256)
