@@ -97,17 +97,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the sources of the four stage kernels (interior, shell, PML face, PML)
+STAGE_SOURCES = ("fwi_interior.cu", "fwi_internal.h", "fwi_pml.cu", "fwi_stage.cu")
+
+
 def kernel_sources_sha256():
-    """Digest of the CUDA sources: a committed ncu traffic figure is reported only
-    while the kernels it was measured on are unchanged."""
+    """Digest of the stage kernels' sources: a committed ncu traffic figure is reported
+    only while the kernels it was measured on are unchanged."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_1504_08340_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".h")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in STAGE_SOURCES:
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
 
 
@@ -298,6 +301,23 @@ def run_batch_sweep(args):
     return 0
 
 
+def profile_gradient(w, nsteps, repeats):
+    """Short gradient evaluations on the benchmark mesh (1 GB of state, nsteps + 1 history
+    levels of 13 MB) for ncu captures of the adjoint and gradient kernels."""
+    import torch
+
+    w.nsteps = nsteps
+    dev = torch.device("cuda", 0)
+    ctx, obs, _ = setup(w, torch, dev)
+    obs.copy_(torch.tensor(fi.synthetic_traces(nsteps, w.nrec_side ** 2, 7)[None], dtype=torch.float32))
+    for _ in range(repeats):
+        J, _, _ = ctx.adjoint_gradient(obs)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_gradient": w.name, "nsteps": nsteps, "repeats": repeats, "misfit": J}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,6 +338,8 @@ def main():
                          "per stage launch, one line per B")
     ap.add_argument("--sweep-nsteps", type=int, default=100,
                     help="RK4 steps of the shot-batch sweep (the configuration has 3000)")
+    ap.add_argument("--profile-gradient", type=int, default=0, metavar="NSTEPS",
+                    help="profiling aid: run only short gradient evaluations (NSTEPS RK4 steps) on the same mesh")
     args = ap.parse_args()
     if args.shot_batch_sweep:
         args.shot_batches = [int(b) for b in args.shot_batch_sweep.split(",")]
@@ -325,6 +347,8 @@ def main():
     w = workload()
     if args.profile_forward:
         return profile_forward(w, args.profile_forward, max(args.steps, 1))
+    if args.profile_gradient:
+        return profile_gradient(w, args.profile_gradient, max(args.steps, 1))
     if args.impl == "reference":
         return run_reference(args, w)
 

@@ -3,7 +3,7 @@
 // (C.1f)/(C.1g) of arXiv:1504.08340 and the FP64 misfit reduction.
 //
 // Element-wise derivatives at a node use the one-sided / centred 3-point stencils
-// of the 27-node LGL element along each axis (see fwi_stage.cu):
+// of the 27-node LGL element along each axis:
 //   C (odd coordinate): (v[c+1] - v[c-1]) / h
 //   L (element below):  (v[c-2] - 4 v[c-1] + 3 v[c]) / h
 //   R (element above):  (-3 v[c] + 4 v[c+1] - v[c+2]) / h
@@ -14,47 +14,8 @@
 namespace fwi {
 namespace {
 
-enum { kC = 0, kL = 1, kR = 2 };
-
-struct Axis {
-  int ns;       // elements along this axis that contain the node (1 or 2)
-  int type[2];  // side type of each
-  bool rd[2];   // element index along this axis inside the interior range
-};
-
-__device__ __forceinline__ Axis axis_info(int c, int n, int lo, int hi) {
-  Axis a;
-  a.ns = 0;
-  a.type[0] = a.type[1] = kC;
-  a.rd[0] = a.rd[1] = false;
-  if (c & 1) {
-    int e = (c - 1) >> 1;
-    a.type[0] = kC;
-    a.rd[0] = e >= lo && e < hi;
-    a.ns = 1;
-  } else {
-    if (c >= 2) {
-      int e = (c >> 1) - 1;
-      a.type[a.ns] = kL;
-      a.rd[a.ns] = e >= lo && e < hi;
-      a.ns++;
-    }
-    if (c <= n - 3) {
-      int e = c >> 1;
-      a.type[a.ns] = kR;
-      a.rd[a.ns] = e >= lo && e < hi;
-      a.ns++;
-    }
-  }
-  return a;
-}
-
-// element-wise derivative stencil (times h) of field f at index i, axis stride s
-__device__ __forceinline__ float dstc(const float *__restrict__ f, int64_t i, int64_t s, int type) {
-  if (type == kC) return __ldg(f + i + s) - __ldg(f + i - s);
-  if (type == kL) return __ldg(f + i - 2 * s) - 4.f * __ldg(f + i - s) + 3.f * __ldg(f + i);
-  return -3.f * __ldg(f + i) + 4.f * __ldg(f + i + s) - __ldg(f + i + 2 * s);
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __global__ void point_kernel(PointArgs p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,78 +47,132 @@ __global__ void sample_kernel(const float *buf, int64_t stride, int nrec, const 
   tr[(int64_t)b * tstride + i] = buf[(int64_t)b * sstride + (int64_t)(9 + c) * stride + node[r]];
 }
 
-// (C.1f)/(C.1g) at one time level. One thread per interior node; the sum over the
-// interior elements around the node of the element-wise gradients' products.
-__global__ void __launch_bounds__(256) gradient_kernel(Geo g, const float *__restrict__ ws0,
-                                                       const float *__restrict__ uh0, double wdt,
-                                                       double *gl, double *gm, int nshot, int64_t sstride,
-                                                       int64_t hstride) {
-  const int64_t mi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (mi >= g.nmat) return;
-  const int i = (int)(mi % g.m[0]);
-  const int64_t t = mi / g.m[0];
-  const int j = (int)(t % g.m[1]);
-  const int k = (int)(t / g.m[1]);
-  const int I = i + 2 * g.lo[0], J = j + 2 * g.lo[1], K = k + 2 * g.lo[2];
-  const int c3[3] = {I, J, K};
-  const int64_t node = ((int64_t)K * g.n[1] + J) * g.px + I;
-  const int64_t sn[3] = {1, (int64_t)g.px, (int64_t)g.px * g.n[1]};
-  const int64_t sm[3] = {1, (int64_t)g.m[0], (int64_t)g.m[0] * g.m[1]};
-  Axis ax[3] = {axis_info(I, g.n[0], g.lo[0], g.hi[0]), axis_info(J, g.n[1], g.lo[1], g.hi[1]),
-                axis_info(K, g.n[2], g.lo[2], g.hi[2])};
-  float W = g.wdetj;
+// (C.1f)/(C.1g) at one time level, in FP64: for every interior node, the sum over the
+// interior elements around it of W detJ times the products of the element-wise
+// gradients of w and u. A block owns a 32 x 8 tile of interior nodes in
+// (x, y) and marches up a chunk of kGKC levels in z. Plane k of the six fields (w and
+// u, three components each) is staged with its two-node x/y halo in a six-slot ring
+// by 4-byte cp.async; the copies of plane k + 3 are in flight while level k is
+// computed from planes k-2 .. k+2, so a level costs one barrier. Every derivative
+// candidate of an axis (C, or L and R) is formed from the five staged values and the
+// one the node's parity asks for is selected, so the x parity alternating across a
+// warp costs no divergence in the stencils.
+constexpr int kGX = 32, kGY = 8, kGKC = 16, kGH = 2;
+constexpr int kGW = kGX + 2 * kGH, kGR = kGY + 2 * kGH, kGP = kGW * kGR;  // staged positions per plane
+constexpr int kGSlots = 6, kGFields = 6;
+constexpr size_t kGSmem = sizeof(float) * kGSlots * kGFields * kGP;
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// copies of plane k (0 <= k < m[2]) of the tile at (x0, y0) into its ring slot; halo
+// positions outside the interior grid are zero-filled (the stencils never select them)
+__device__ __forceinline__ void grad_stage_plane(const Geo &g, const float *ws, const float *uh, float *ring, int k,
+                                                 int x0, int y0, int tid) {
+  float *slot = ring + ((k + kGSlots) % kGSlots) * (kGFields * kGP);
+  for (int p = tid; p < kGP; p += kGX * kGY) {
+    const int hy = p / kGW, hx = p - hy * kGW;
+    const int i = x0 - kGH + hx, j = y0 - kGH + hy;
+    const bool v = i >= 0 && i < g.m[0] && j >= 0 && j < g.m[1];
+    const int64_t node =
+        v ? ((int64_t)(k + 2 * g.lo[2]) * g.n[1] + (j + 2 * g.lo[1])) * g.px + (i + 2 * g.lo[0]) : 0;
+    const int64_t mi = v ? ((int64_t)k * g.m[1] + j) * g.m[0] + i : 0;
 #pragma unroll
-  for (int x = 0; x < 3; x++) W *= (c3[x] & 1) ? (4.f / 3.f) : (1.f / 3.f);
-  double accl = gl[mi], accm = gm[mi];
-  // the shots of a batch in order: shot b's adjoint state at ws0 + b sstride, its
-  // displacement history level at uh0 + b hstride
+    for (int c = 0; c < 3; c++) {
+      cp_async4(slot + c * kGP + p, ws + (int64_t)(9 + c) * g.stride + node, v ? 4 : 0);
+      cp_async4(slot + (3 + c) * kGP + p, uh + (int64_t)c * g.nmat + mi, v ? 4 : 0);
+    }
+  }
+}
+
+// the candidates of one axis from the five values f[-2..2] along it: side 0 is C (odd
+// coordinate) or L (even), side 1 is R
+__device__ __forceinline__ void grad_axis(float a, float b, float c, float d, float e, bool odd, float inv_h,
+                                          float &s0, float &s1) {
+  s0 = (odd ? d - b : a - 4.f * b + 3.f * c) * inv_h;
+  s1 = (-3.f * c + 4.f * d - e) * inv_h;
+}
+
+__global__ void __launch_bounds__(kGX *kGY, 3) gradient_kernel(Geo g, const float *__restrict__ ws0,
+                                                                     const float *__restrict__ uh0, double wdt,
+                                                                     double *gl, double *gm, int nshot,
+                                                                     int64_t sstride, int64_t hstride) {
+  extern __shared__ float ring[];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kGX + tx;
+  const int x0 = blockIdx.x * kGX, y0 = blockIdx.y * kGY, k0 = blockIdx.z * kGKC;
+  const int m2 = g.m[2], k1 = min(k0 + kGKC, m2);
+  const int i = x0 + tx, j = y0 + ty;
+  const bool own = i < g.m[0] && j < g.m[1];
+  // element sides present along each axis: odd coordinate -> the one element it is
+  // the centre of; even -> below (L) if it is not the first node, above (R) if it is
+  // not the last
+  const bool ox = i & 1, oy = j & 1;
+  const bool vx[2] = {ox || i >= 2, !ox && i <= g.m[0] - 3};
+  const bool vy[2] = {oy || j >= 2, !oy && j <= g.m[1] - 3};
+  const float Wxy = g.wdetj * (ox ? 4.f / 3.f : 1.f / 3.f) * (oy ? 4.f / 3.f : 1.f / 3.f);
+  const int q = (ty + kGH) * kGW + tx + kGH;  // the node's staged position
 #pragma unroll 1
   for (int b = 0; b < nshot; b++) {
-  const float *__restrict__ ws = ws0 + b * sstride;
-  const float *__restrict__ uh = uh0 + b * hstride;
-  // all loops have fixed trip counts and are unrolled, so the arrays stay in registers
-  float dw[3][2][3], du[3][2][3];  // [axis][side][component]
+    const float *ws = ws0 + b * sstride;
+    const float *uh = uh0 + b * hstride;
+    for (int k = max(k0 - 2, 0); k <= min(k0 + 2, m2 - 1); k++) grad_stage_plane(g, ws, uh, ring, k, x0, y0, tid);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 1
+    for (int k = k0; k < k1; k++) {
+      if (k + 3 <= min(k1 + 1, m2 - 1)) grad_stage_plane(g, ws, uh, ring, k + 3, x0, y0, tid);
+      cp_async_commit();
+      if (own) {
+        const bool oz = k & 1;
+        const bool vz[2] = {oz || k >= 2, !oz && k <= m2 - 3};
+        const float *sl5[5];
 #pragma unroll
-  for (int x = 0; x < 3; x++)
+        for (int d = 0; d < 5; d++) sl5[d] = ring + ((k - 2 + d + kGSlots) % kGSlots) * (kGFields * kGP) + q;
+        float dv[3][2][kGFields];  // [axis][side][field]
 #pragma unroll
-    for (int s = 0; s < 2; s++) {
-      const bool used = s < ax[x].ns && ax[x].rd[s];
+        for (int f = 0; f < kGFields; f++) {
+          const float *c = sl5[2] + f * kGP;
+          grad_axis(c[-2], c[-1], c[0], c[1], c[2], ox, g.inv_h, dv[0][0][f], dv[0][1][f]);
+          grad_axis(c[-2 * kGW], c[-kGW], c[0], c[kGW], c[2 * kGW], oy, g.inv_h, dv[1][0][f], dv[1][1][f]);
+          grad_axis(sl5[0][f * kGP], sl5[1][f * kGP], c[0], sl5[3][f * kGP], sl5[4][f * kGP], oz, g.inv_h,
+                    dv[2][0][f], dv[2][1][f]);
+        }
+        float sl = 0.f, smu = 0.f;
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        dw[x][s][c] = used ? dstc(ws + (int64_t)(9 + c) * g.stride, node, sn[x], ax[x].type[s]) * g.inv_h : 0.f;
-        du[x][s][c] = used ? dstc(uh + (int64_t)c * g.nmat, mi, sm[x], ax[x].type[s]) * g.inv_h : 0.f;
+        for (int sx = 0; sx < 2; sx++)
+#pragma unroll
+          for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+            for (int sz = 0; sz < 2; sz++) {
+              if (!(vx[sx] && vy[sy] && vz[sz])) continue;
+              const int sd[3] = {sx, sy, sz};
+              float Gw[3][3], Gu[3][3];  // G[a][b] = d v_a / d x_b
+#pragma unroll
+              for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int x = 0; x < 3; x++) {
+                  Gw[a][x] = dv[x][sd[x]][a];
+                  Gu[a][x] = dv[x][sd[x]][3 + a];
+                }
+              const float divw = Gw[0][0] + Gw[1][1] + Gw[2][2];
+              const float divu = Gu[0][0] + Gu[1][1] + Gu[2][2];
+              sl += divw * divu;
+              smu += 2.f * (Gw[0][0] * Gu[0][0] + Gw[1][1] * Gu[1][1] + Gw[2][2] * Gu[2][2]) +
+                     (Gw[0][1] + Gw[1][0]) * (Gu[1][0] + Gu[0][1]) + (Gw[0][2] + Gw[2][0]) * (Gu[2][0] + Gu[0][2]) +
+                     (Gw[1][2] + Gw[2][1]) * (Gu[2][1] + Gu[1][2]);
+            }
+        const float W = Wxy * (oz ? 4.f / 3.f : 1.f / 3.f);
+        const int64_t mi = ((int64_t)k * g.m[1] + j) * g.m[0] + i;
+        gl[mi] -= wdt * (double)W * (double)sl;
+        gm[mi] -= wdt * (double)W * (double)smu;
       }
+      cp_async_wait_all();
+      __syncthreads();
     }
-  float sl = 0.f, smu = 0.f;
-#pragma unroll
-  for (int sx = 0; sx < 2; sx++)
-#pragma unroll
-    for (int sy = 0; sy < 2; sy++)
-#pragma unroll
-      for (int sz = 0; sz < 2; sz++) {
-        if (sx >= ax[0].ns || sy >= ax[1].ns || sz >= ax[2].ns) continue;
-        if (!(ax[0].rd[sx] && ax[1].rd[sy] && ax[2].rd[sz])) continue;
-        const int s[3] = {sx, sy, sz};
-        float Gw[3][3], Gu[3][3];  // G[i][j] = d v_i / d x_j
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-          for (int b = 0; b < 3; b++) {
-            Gw[a][b] = dw[b][s[b]][a];
-            Gu[a][b] = du[b][s[b]][a];
-          }
-        const float divw = Gw[0][0] + Gw[1][1] + Gw[2][2];
-        const float divu = Gu[0][0] + Gu[1][1] + Gu[2][2];
-        sl += divw * divu;
-        smu += 2.f * (Gw[0][0] * Gu[0][0] + Gw[1][1] * Gu[1][1] + Gw[2][2] * Gu[2][2]) +
-               (Gw[0][1] + Gw[1][0]) * (Gu[1][0] + Gu[0][1]) + (Gw[0][2] + Gw[2][0]) * (Gu[2][0] + Gu[0][2]) +
-               (Gw[1][2] + Gw[2][1]) * (Gu[2][1] + Gu[1][2]);
-      }
-  accl -= wdt * (double)W * (double)sl;
-  accm -= wdt * (double)W * (double)smu;
   }
-  gl[mi] = accl;
-  gm[mi] = accm;
 }
 
 constexpr int kRedThreads = 256;
@@ -223,8 +238,15 @@ void launch_sample(const float *buf, int64_t stride, int nrec, const int64_t *no
 
 void launch_gradient(const Geo &g, const float *w_state, const float *u_hist, double wdt, double *gl,
                      double *gm, cudaStream_t s, int nshot, int64_t sstride, int64_t hstride) {
-  gradient_kernel<<<blocks_for(g.nmat, 256), 256, 0, s>>>(g, w_state, u_hist, wdt, gl, gm, nshot, sstride,
-                                                          hstride);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
+    attr = true;
+  }
+  const dim3 grid((g.m[0] + kGX - 1) / kGX, (g.m[1] + kGY - 1) / kGY, (g.m[2] + kGKC - 1) / kGKC);
+  gradient_kernel<<<grid, dim3(kGX, kGY), kGSmem, s>>>(g, w_state, u_hist, wdt, gl, gm, nshot, sstride,
+                                                             hstride);
+
 }
 
 int misfit_blocks(int64_t n) {
