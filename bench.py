@@ -97,8 +97,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# the sources of the four stage kernels (interior, shell, PML face, PML)
-STAGE_SOURCES = ("fwi_interior.cu", "fwi_internal.h", "fwi_pml.cu", "fwi_stage.cu")
+# the sources of the four stage kernels (interior, shell, PML face, PML) and of the host
+# code that builds their node lists and launch shapes
+STAGE_SOURCES = ("fwi_api.cu", "fwi_interior.cu", "fwi_internal.h", "fwi_pml.cu", "fwi_stage.cu")
 
 
 def kernel_sources_sha256():

@@ -126,3 +126,46 @@ def test_shot_batch_rejects_bad_sizes():
             with pytest.raises(Exception):
                 ctx.set_shot_batch(bad)
         ctx.set_shot_batch(1024 // 256)
+
+
+def test_layered_96x96x48_full_size_batched(oracle_mod):
+    """The 16-shot layered 96x96x48 + 10 PML mesh (48x48 receivers) at full size, in the
+    launch configuration of the shot-batch benchmark: B = 16 against B = 1 over all 16
+    shots (traces bitwise, J equal, gradients to 1e-12), and one shot of the batch against
+    the FP64 oracle over 4 steps (a Ricker centred at t = 0, so the first steps carry
+    signal; seeded synthetic observed traces)."""
+    from paper_1504_08340_gb300 import Context
+
+    w = fi.layered_96x96x48()
+    w.nsteps = 4
+    wp = (w.f0, 0.0, w.amp)
+    lam, mu = (_f32(a) for a in fi.medium(w, "true"))
+    src, dirs, rec = w.sources(), w.source_dirs(), w.receivers()
+    obs = _f32(np.stack([fi.synthetic_traces(w.nsteps, len(rec), 200 + s) for s in range(w.nshots)]))
+    with Context(w.nx, w.ny, w.nz, w.npml, w.h, w.dt, w.nsteps, rho=w.rho) as ctx:
+        ctx.set_material(lam, mu)
+        ctx.set_sources(src, dirs, "ricker", wp)
+        ctx.set_receivers(rec)
+        obs_d = torch.tensor(obs, device="cuda")
+        ctx.set_shot_batch(16)
+        tr16 = ctx.forward(0, w.nshots)
+        J16, gl16, gm16 = ctx.adjoint_gradient(obs_d, 0, w.nshots)
+        gl16, gm16 = gl16.cpu().numpy(), gm16.cpu().numpy()
+        ctx.set_shot_batch(1)
+        tr1 = ctx.forward(0, w.nshots)
+        J1, gl1, gm1 = ctx.adjoint_gradient(obs_d, 0, w.nshots)
+        s = 5
+        Js, gls, gms = ctx.adjoint_gradient(obs_d[s:s + 1], s, 1)
+    assert np.array_equal(tr16, tr1) and J16 == J1
+    assert rel_l2(gl16, gl1.cpu().numpy()) < 1e-12 and rel_l2(gm16, gm1.cpu().numpy()) < 1e-12
+    o = oracle_mod.Oracle(w.nx, w.ny, w.nz, w.npml, h=w.h, rho=w.rho)
+    o.set_material(lam.astype(np.float64), mu.astype(np.float64))
+    sn = [o.node_id(*src[s])]
+    rn = [o.node_id(*r) for r in rec]
+    J_o, gl_o, gm_o, tr_o = o.misfit_and_gradient(w.dt, w.nsteps, sn, dirs[s:s + 1], rn,
+                                                  obs[s].astype(np.float64), "ricker", wp)
+    assert np.abs(tr_o).max() > 0
+    assert rel_l2(tr16[s], tr_o) < 1e-5
+    assert Js == pytest.approx(J_o, rel=2e-5)
+    assert rel_l2(gls.cpu().numpy().ravel(), gl_o.ravel()) < 1e-4
+    assert rel_l2(gms.cpu().numpy().ravel(), gm_o.ravel()) < 1e-4
