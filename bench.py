@@ -298,6 +298,11 @@ def run_batch_sweep(args):
                          "avg_launch_ms": stage_ms / max(stage_launches, 1)},
             "gpu_launches": int(all_launches), "misfit": J, "J_equal_to_B1": J == ref[0],
             "gradient_rel_l2_vs_B1": drift, "clocks": clocks}), flush=True)
+    # the library's own choice: fwi_tune_shot_batch times 10 forward steps per candidate
+    t0 = time.perf_counter()
+    chosen = ctx.tune_shot_batch(0, w.nshots, max_batch=max(args.shot_batches), steps=10)
+    print(json.dumps({"autotune": {"chosen_shot_batch": chosen, "max_batch": max(args.shot_batches),
+                                   "steps_per_candidate": 10, "seconds": time.perf_counter() - t0}}), flush=True)
     ctx.close()
     return 0
 

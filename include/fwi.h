@@ -241,6 +241,22 @@ fwi_status fwi_set_checkpointing(fwi_ctx *ctx, int interval);
  * changes. Errors: FWI_E_INVAL (B outside [1, 1024]), FWI_E_NOMEM. */
 fwi_status fwi_set_shot_batch(fwi_ctx *ctx, int batch);
 
+/* Picks the shot batch B by measurement and leaves the context at it (as
+ * fwi_set_shot_batch). Candidates are B = 1, 2, 4, ... below, and equal to, the
+ * largest B that is at most max_batch and nshots and whose per-shot buffers for a
+ * gradient evaluation (RK4 state sets, traces, and the history, snapshots and
+ * recompute sets of the current checkpointing mode) fit in mem_fraction of the
+ * device memory that is free or held by this context's per-shot buffers. Each
+ * candidate runs one untimed and `steps` timed forward RK4 steps of the shots
+ * shot0 .. shot0 + B - 1 (CUDA events on the context's stream); a larger B is kept
+ * only if it advances at least 2 % more shot-steps per second.
+ *   chosen (host): the B picked.
+ * The context's RK4 state is cleared. Errors: FWI_E_STATE (material, sources or
+ * receivers not set), FWI_E_INVAL (shot range, max_batch < 1, steps outside
+ * [1, nsteps), mem_fraction outside (0, 1], null chosen), FWI_E_NOMEM, FWI_E_CUDA. */
+fwi_status fwi_tune_shot_batch(fwi_ctx *ctx, int shot0, int nshots, int max_batch, int steps, double mem_fraction,
+                               int *chosen);
+
 /* Current material ([k][j][i] as in fwi_set_material; host or device). */
 fwi_status fwi_get_material(fwi_ctx *ctx, float *lambda, float *mu, int on_device);
 

@@ -306,6 +306,7 @@ fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot0, int nb, float *hist_
 
 fwi_status require_ready(fwi_ctx *c, int shot0, int nshots) {
   TRY(check_stream(c));
+  if (!c->state[0]) return fail(c, FWI_E_STATE, "no RK4 state buffers (a shot batch allocation failed)");
   if (!c->have_material) return fail(c, FWI_E_STATE, "material not set");
   if (c->nshots <= 0) return fail(c, FWI_E_STATE, "sources not set");
   if (c->nrec <= 0) return fail(c, FWI_E_STATE, "receivers not set");
@@ -1243,6 +1244,7 @@ fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int
   TRY(check_stream(c));
   if (!c->have_material) return fail(c, FWI_E_STATE, "material not set");
   if (!state || !rate) return fail(c, FWI_E_INVAL, "null argument");
+  if (!c->state[0]) return fail(c, FWI_E_STATE, "no RK4 state buffers (a shot batch allocation failed)");
   const size_t n = (size_t)fwi::kFields * c->geo.stride;
   const float *in = state;
   float *out = rate;
@@ -1296,26 +1298,114 @@ fwi_status fwi_regularization(fwi_ctx *c, int kind, double eps, double *R, doubl
   return FWI_OK;
 }
 
-fwi_status fwi_set_shot_batch(fwi_ctx *c, int batch) {
-  if (!c) return FWI_E_INVAL;
-  TRY(check_stream(c));
-  if (batch < 1 || batch > 1024) return fail(c, FWI_E_INVAL, "shot batch %d outside [1, 1024]", batch);
-  if (batch == c->batch) return FWI_OK;
+namespace {
+
+// drop every buffer sized by the shot batch and allocate the RK4 state sets for B shots;
+// on failure the context falls back to B = 1 (or, if even that fails, holds no state
+// sets, which require_ready reports)
+fwi_status resize_batch(fwi_ctx *c, int batch) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  // every per-shot buffer is sized by the batch: drop them all, then the state sets again
   for (int b = 0; b < 4; b++) {
     dfree(c->state[b]);
     dfree(c->rstate[b]);
   }
   for (float **p : {&c->d_snap, &c->d_hist, &c->d_traces, &c->d_obs, &c->d_resid}) dfree(*p);
   c->snap_cap = c->hist_cap = 0;
-  c->batch = batch;
-  const size_t n = set_floats(c) * batch;
-  for (int b = 0; b < 4; b++) {
-    TRY(dalloc(c, &c->state[b], n));
-    CUDA_TRY(c, cudaMemsetAsync(c->state[b], 0, n * sizeof(float), c->stream));
+  fwi_status st = FWI_OK;
+  for (int attempt = 0; attempt < 2; attempt++) {
+    c->batch = attempt == 0 ? batch : 1;
+    const size_t n = set_floats(c) * c->batch;
+    st = FWI_OK;
+    for (int b = 0; b < 4 && st == FWI_OK; b++) {
+      st = dalloc(c, &c->state[b], n);
+      if (st == FWI_OK && cudaMemsetAsync(c->state[b], 0, n * sizeof(float), c->stream) != cudaSuccess)
+        st = fail(c, FWI_E_CUDA, "state clear failed");
+    }
+    if (st == FWI_OK) break;
+    for (int b = 0; b < 4; b++) dfree(c->state[b]);
   }
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (st == FWI_OK && c->batch != batch) st = fail(c, FWI_E_NOMEM, "no memory for a batch of %d shots", batch);
+  const cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (st == FWI_OK && e != cudaSuccess) st = fail(c, FWI_E_CUDA, "%s", cudaGetErrorString(e));
+  return st;
+}
+
+// device bytes one shot of a batch needs for a gradient evaluation in the current
+// checkpointing mode: RK4 state sets, history, snapshots and recompute sets, traces
+size_t bytes_per_shot(const fwi_ctx *c) {
+  const int N = c->cfg.nsteps;
+  int every = c->ckpt < 0 ? (int)std::ceil(std::sqrt((double)N)) : c->ckpt;
+  if (every >= N) every = 0;
+  size_t f = 4 * set_floats(c) + 3 * trace_floats(c);
+  if (every == 0)
+    f += (size_t)(N + 1) * level_floats(c);
+  else
+    f += (size_t)(every + 1) * level_floats(c) + (size_t)((N + every - 1) / every + 4) * set_floats(c);
+  return f * sizeof(float);
+}
+
+}  // namespace
+
+fwi_status fwi_set_shot_batch(fwi_ctx *c, int batch) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (batch < 1 || batch > 1024) return fail(c, FWI_E_INVAL, "shot batch %d outside [1, 1024]", batch);
+  if (batch == c->batch && c->state[0]) return FWI_OK;
+  return resize_batch(c, batch);
+}
+
+fwi_status fwi_tune_shot_batch(fwi_ctx *c, int shot0, int nshots, int max_batch, int steps, double mem_fraction,
+                               int *chosen) {
+  if (!c) return FWI_E_INVAL;
+  TRY(require_ready(c, shot0, nshots));
+  if (!chosen || max_batch < 1 || steps < 1 || steps >= c->cfg.nsteps || !(mem_fraction > 0 && mem_fraction <= 1))
+    return fail(c, FWI_E_INVAL, "invalid tuning arguments");
+  // memory cap: what is free plus what this context's per-shot buffers hold now
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
+  size_t held = (size_t)4 * set_floats(c) * c->batch + c->hist_cap * level_floats(c) + c->snap_cap * set_floats(c);
+  if (c->rstate[0]) held += (size_t)4 * set_floats(c) * c->batch;
+  if (c->d_traces) held += (size_t)3 * trace_floats(c) * c->batch;
+  held *= sizeof(float);
+  const double avail = mem_fraction * (double)(free_b + held);
+  int bmax = (int)std::min<double>(avail / (double)bytes_per_shot(c), 1024.0);
+  bmax = std::min(std::min(bmax, max_batch), nshots);
+  if (bmax < 1) bmax = 1;
+  std::vector<int> cand;
+  for (int b = 1; b < bmax; b *= 2) cand.push_back(b);
+  cand.push_back(bmax);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, FWI_E_CUDA, "event creation failed");
+  }
+  int best = 1;
+  double best_rate = -1.0;
+  fwi_status st = FWI_OK;
+  for (size_t q = 0; q < cand.size() && st == FWI_OK; q++) {
+    const int B = cand[q];
+    st = resize_batch(c, B);
+    // one untimed step, then `steps` timed forward RK4 steps of shots shot0 .. shot0 + B - 1
+    if (st == FWI_OK) st = rk4_step(c, false, 0, shot0, B, nullptr, 0);
+    if (st == FWI_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, FWI_E_CUDA, "event record failed");
+    for (int n = 1; n <= steps && st == FWI_OK; n++) st = rk4_step(c, false, n, shot0, B, nullptr, 0);
+    float ms = 0.f;
+    if (st == FWI_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = fail(c, FWI_E_CUDA, "tuning timing failed");
+    if (st != FWI_OK) break;
+    // shot-steps per second; a larger batch has to be 2 % faster to be kept (memory)
+    const double rate = (double)B * steps / (ms * 1e-3);
+    if (rate > 1.02 * best_rate) {
+      best = B;
+      best_rate = rate;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TRY(st);
+  TRY(resize_batch(c, best));
+  *chosen = best;
   return FWI_OK;
 }
 

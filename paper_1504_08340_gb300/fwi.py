@@ -53,7 +53,7 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
            "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization",
-           "fwi_set_shot_batch")
+           "fwi_set_shot_batch", "fwi_tune_shot_batch")
 
 _lib = None
 
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_get_material.argtypes = [P, P, P, I]
     lib.fwi_set_checkpointing.argtypes = [P, I]
     lib.fwi_set_shot_batch.argtypes = [P, I]
+    lib.fwi_tune_shot_batch.argtypes = [P, I, I, I, I, C.c_double, C.POINTER(I)]
     lib.fwi_regularization.argtypes = [P, I, C.c_double, D, P, P, I]
     for name in EXPORTS:
         if name not in ("fwi_destroy", "fwi_last_error", "fwi_status_string"):
@@ -293,6 +294,15 @@ class Context:
     def set_shot_batch(self, batch):
         """Shots advanced together by one launch of each stage kernel (fwi_set_shot_batch)."""
         self._check(self.lib.fwi_set_shot_batch(self.ptr, int(batch)))
+
+    def tune_shot_batch(self, shot0=0, nshots=None, max_batch=64, steps=10, mem_fraction=0.8):
+        """Pick the shot batch by timing forward steps per candidate (fwi_tune_shot_batch); returns it."""
+        if nshots is None:
+            nshots = self.nshots - shot0
+        b = C.c_int()
+        self._check(self.lib.fwi_tune_shot_batch(self.ptr, int(shot0), int(nshots), int(max_batch), int(steps),
+                                                 float(mem_fraction), C.byref(b)))
+        return b.value
 
     def set_checkpointing(self, interval):
         """0: store u at every step; k > 0: snapshot every k steps and recompute;

@@ -169,3 +169,24 @@ def test_layered_96x96x48_full_size_batched(oracle_mod):
     assert Js == pytest.approx(J_o, rel=2e-5)
     assert rel_l2(gls.cpu().numpy().ravel(), gl_o.ravel()) < 1e-4
     assert rel_l2(gms.cpu().numpy().ravel(), gm_o.ravel()) < 1e-4
+
+
+def test_tune_shot_batch():
+    """The tuner picks one of its candidates (1, 2, 4 for four shots), leaves the context
+    at it with results unchanged, honours max_batch, and rejects bad arguments."""
+    w = _workload(nsteps=30)
+    ctx, obs, _, _ = _setup(w)
+    with ctx:
+        ref = ctx.forward(0, w.nshots)
+        J1 = ctx.misfit(obs, 0, w.nshots)
+        B = ctx.tune_shot_batch(0, w.nshots, max_batch=8, steps=5)
+        assert B in (1, 2, 4)
+        assert np.array_equal(ctx.forward(0, w.nshots), ref)
+        assert ctx.misfit(obs, 0, w.nshots) == J1
+        assert ctx.tune_shot_batch(1, 3, max_batch=1, steps=3) == 1
+        good = dict(max_batch=4, steps=3, mem_fraction=0.8)
+        for bad in (dict(steps=0), dict(steps=30), dict(max_batch=0), dict(mem_fraction=0.0),
+                    dict(mem_fraction=1.5)):
+            with pytest.raises(Exception):
+                ctx.tune_shot_batch(0, w.nshots, **{**good, **bad})
+        assert np.array_equal(ctx.forward(0, w.nshots), ref)
