@@ -360,6 +360,8 @@ def main():
 
     import torch
 
+    from paper_1504_08340_gb300.distributed import max_over_ranks
+
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -402,10 +404,7 @@ def main():
     stage_ms, stage_launches = ctx.timing(0)
     grad_ms, grad_launches = ctx.timing(1)
     _, all_launches = ctx.timing(3)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, device=dev)
     value = world / (ms_max / 1e3)
 
     hbm, peak_kind = _peaks()
@@ -430,10 +429,7 @@ def main():
             Je, _, _ = ctx.adjoint_gradient(on, g_lambda=gln, g_mu=gmn)
         barrier()
         te = (time.perf_counter() - t0) / args.steps
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world / float(tt.item()), "unit": UNIT,
+        e2e = {"value": world / max_over_ranks(te, device=dev), "unit": UNIT,
                "h2d_bytes_per_step": int(on.nbytes + mn.nbytes + mu_h.numpy().nbytes),
                "d2h_bytes_per_step": int(gln.nbytes + gmn.nbytes + 8)}
         assert abs(Je - J) <= 1e-12 * abs(J)

@@ -1,0 +1,84 @@
+"""The shot-parallel reduction over CPU ranks (gloo): the summed misfit and gradients
+equal, bitwise and on every rank, the single-process sum of the per-rank parts in
+rank order; the shot ranges tile the shot list; timing takes the max over ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+dist = pytest.importorskip("torch.distributed")
+
+from paper_1504_08340_gb300.distributed import max_over_ranks, reduce_gradient, shot_range  # noqa: E402
+
+SHAPE = (5, 7, 9)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _part(rank):
+    """Seeded per-rank misfit and gradients, with magnitudes far apart so that the
+    order of the sum shows in the last bits."""
+    rng = np.random.default_rng(100 + rank)
+    scale = 10.0 ** (3 * rank)
+    gl = torch.tensor(scale * rng.standard_normal(SHAPE), dtype=torch.float64)
+    gm = torch.tensor(scale * rng.standard_normal(SHAPE), dtype=torch.float64)
+    return float(scale * rng.random()), gl, gm
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        J, gl, gm = _part(rank)
+        Js, gls, gms = reduce_gradient(J, gl, gm)
+        tmax = max_over_ranks(1.5 + rank)
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), J=Js, gl=gls.numpy(), gm=gms.numpy(), tmax=tmax)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_reduce_gradient_is_the_rank_order_sum(tmp_path, world):
+    import torch.multiprocessing as mp
+
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    parts = [_part(r) for r in range(world)]
+    J_ref, gl_ref, gm_ref = parts[0][0], parts[0][1].clone(), parts[0][2].clone()
+    for J, gl, gm in parts[1:]:
+        J_ref += J
+        gl_ref += gl
+        gm_ref += gm
+    for r in range(world):
+        got = np.load(tmp_path / f"rank{r}.npz")
+        assert float(got["J"]) == J_ref
+        assert np.array_equal(got["gl"], gl_ref.numpy()) and np.array_equal(got["gm"], gm_ref.numpy())
+        assert float(got["tmax"]) == 1.5 + (world - 1)
+
+
+def test_reduce_without_process_group_is_identity():
+    J, gl, gm = _part(0)
+    Jr, glr, gmr = reduce_gradient(J, gl, gm)
+    assert Jr == J and glr is gl and gmr is gm
+    assert max_over_ranks(2.5) == 2.5
+
+
+@pytest.mark.parametrize("nshots,world", [(16, 1), (16, 2), (16, 3), (64, 8), (5, 8), (0, 2)])
+def test_shot_ranges_tile_the_shots(nshots, world):
+    ranges = [shot_range(nshots, r, world) for r in range(world)]
+    covered = [s for s0, n in ranges for s in range(s0, s0 + n)]
+    assert covered == list(range(nshots))
+    counts = [n for _, n in ranges]
+    assert max(counts) - min(counts) <= 1
+
+
+def test_shot_range_rejects_bad_arguments():
+    for args in ((4, 2, 2), (4, -1, 2), (4, 0, 0), (-1, 0, 1)):
+        with pytest.raises(ValueError):
+            shot_range(*args)

@@ -190,3 +190,24 @@ def test_tune_shot_batch():
             with pytest.raises(Exception):
                 ctx.tune_shot_batch(0, w.nshots, **{**good, **bad})
         assert np.array_equal(ctx.forward(0, w.nshots), ref)
+
+
+def test_sharded_gradient_matches_all_shots():
+    """One rank's sharded evaluation is the whole-range call; two ranks' shares, summed
+    in rank order, give the whole-range misfit and gradients up to the order of the FP64
+    sums over the shots."""
+    from paper_1504_08340_gb300.distributed import sharded_adjoint_gradient, shot_range
+
+    w = _workload(nsteps=30)
+    ctx, obs, _, _ = _setup(w)
+    with ctx:
+        J, gl, gm = ctx.adjoint_gradient(obs, 0, w.nshots)
+        Js, gls, gms = sharded_adjoint_gradient(ctx, obs, w.nshots, 0, 1)
+        assert Js == J and torch.equal(gls, gl) and torch.equal(gms, gm)
+        parts = []
+        for r in range(2):
+            s0, n = shot_range(w.nshots, r, 2)
+            parts.append(ctx.adjoint_gradient(obs[s0:s0 + n], s0, n))
+    assert parts[0][0] + parts[1][0] == pytest.approx(J, rel=1e-12)
+    assert rel_l2((parts[0][1] + parts[1][1]).cpu().numpy(), gl.cpu().numpy()) < 1e-12
+    assert rel_l2((parts[0][2] + parts[1][2]).cpu().numpy(), gm.cpu().numpy()) < 1e-12
