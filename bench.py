@@ -324,6 +324,82 @@ def profile_gradient(w, nsteps, repeats):
     return 0
 
 
+# FP32 CUDA-core peak of a GB300 at its 2070 MHz maximum clock: 152 SMs x 128 FP32 lanes x
+# 2 flops per fused multiply-add (the bound of the direct convolutions, which do not use
+# tensor cores)
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_precond_bench(args):
+    """The learned preconditioner's 3x3x3 convolution kernels on the interior material grid of
+    the 64x64x32 mesh (65 x 129 x 129 voxels), 32 -> 32 channels, BF16 activations and
+    weights with FP32 accumulation (inputs larger than L2), and one training step of a
+    4 -> 16 -> 16 -> 2 network on the same grid. One JSON line per kernel."""
+    import ctypes
+
+    import torch
+
+    from paper_1504_08340_gb300.fwi import load_library
+    from paper_1504_08340_gb300.precond import ConvNet
+
+    lib = load_library()
+    dev = torch.device("cuda", 0)
+    D, H, W = fi.grf_64x64x32().mat_shape
+    nv = D * H * W
+    c = 32
+    g = torch.Generator(device=dev).manual_seed(0)
+    x32 = torch.randn((c, D, H, W), generator=g, device=dev)
+    net = ConvNet((4, 16, 16, 2), (D, H, W), seed=0, device=dev)
+    x = net.to_bf16(x32)
+    w = net.to_bf16(torch.randn((c, c, 27), generator=g, device=dev) / (27 * c) ** 0.5)
+    b = torch.zeros(c, device=dev)
+    y = torch.empty((c, D, H, W), dtype=torch.bfloat16, device=dev)
+    dy = torch.randn((c, D, H, W), generator=g, device=dev)
+    dx = torch.empty_like(dy)
+    dw = torch.empty((c, c, 27), device=dev)
+    db = torch.empty(c, device=dev)
+    work = torch.empty(lib.fwi_nn_conv3d_backward_weight_work(c, c, D, H, W), device=dev)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    kernels = {
+        "conv3d_forward (ReLU)": lambda: lib.fwi_nn_conv3d_forward(P(x), P(w), P(b), c, c, D, H, W, 1, P(y), st),
+        "conv3d_backward_data": lambda: lib.fwi_nn_conv3d_backward_data(P(dy), P(w), c, c, D, H, W, P(dx), st),
+        "conv3d_backward_weight": lambda: lib.fwi_nn_conv3d_backward_weight(P(dy), P(x), c, c, D, H, W, P(dw), P(db),
+                                                                            P(work), st),
+    }
+    flops = 2.0 * c * c * 27 * nv
+    for name, fn in kernels.items():
+        for _ in range(max(args.warmup, 3)):
+            assert fn() == 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            assert fn() == 0
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        tf = flops / (ms * 1e-3) / 1e12
+        print(json.dumps({"metric": "learned preconditioner kernel", "kernel": name, "ms_per_launch": ms,
+                          "TFLOP/s": tf, "dtype": "bf16 storage, f32 accumulate", "data": "synthetic",
+                          "config": {"grid": [D, H, W], "channels": [c, c], "l2": "inputs larger than L2"},
+                          "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                                       "frac": tf / FP32_ALU_TFLOPS, "peak_kind": "derived (FP32 lanes x clock)"}}),
+              flush=True)
+    inp = torch.randn((4, D, H, W), generator=g, device=dev)
+    target = torch.randn((2, D, H, W), generator=g, device=dev)
+    xb = net.to_bf16(inp)
+    for _ in range(2):
+        net.train_step(xb, target)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = [net.train_step(xb, target) for _ in range(args.steps)]
+    sec = (time.perf_counter() - t0) / args.steps
+    print(json.dumps({"metric": "learned preconditioner training step", "network": "4-16-16-2, 3x3x3 convolutions",
+                      "grid": [D, H, W], "seconds_per_step": sec, "loss_first": losses[0], "loss_last": losses[-1]}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,7 +422,11 @@ def main():
                     help="RK4 steps of the shot-batch sweep (the configuration has 3000)")
     ap.add_argument("--profile-gradient", type=int, default=0, metavar="NSTEPS",
                     help="profiling aid: run only short gradient evaluations (NSTEPS RK4 steps) on the same mesh")
+    ap.add_argument("--precond-bench", action="store_true",
+                    help="instead of the headline benchmark: the learned preconditioner's kernels")
     args = ap.parse_args()
+    if args.precond_bench:
+        return run_precond_bench(args)
     if args.shot_batch_sweep:
         args.shot_batches = [int(b) for b in args.shot_batch_sweep.split(",")]
         return run_batch_sweep(args)

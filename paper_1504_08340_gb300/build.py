@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libfwi.so")
-SOURCES = ["fwi_api.cu", "fwi_kernels.cu", "fwi_stage.cu", "fwi_interior.cu", "fwi_pml.cu", "fwi_opt.cu", "fwi_noalloc.cu"]
+SOURCES = ["fwi_api.cu", "fwi_kernels.cu", "fwi_stage.cu", "fwi_interior.cu", "fwi_pml.cu", "fwi_opt.cu", "fwi_noalloc.cu",
+           "fwi_precond.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -23,7 +24,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "fwi.h")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

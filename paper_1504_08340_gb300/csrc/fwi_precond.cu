@@ -1,0 +1,341 @@
+// fwi_precond.cu -- kernels of the learned gradient preconditioner (sm_103a): 3x3x3
+// convolutions forward and backward, ReLU backward, mean squared error and Adam, with
+// BF16 storage of activations and weights and FP32 accumulation (fwi_precond.h).
+//
+// The convolutions are direct: a thread owns one voxel and a block of 8 output (or,
+// backward, input) channels, walks the input channels and the 27 taps, and reads each
+// input value once per tap for its 8 channels. All threads of a warp read the same
+// weight, which L1 broadcasts. Every sum runs in a fixed order (channels, then taps;
+// weight gradients over fixed voxel chunks, then the chunks in order), so results
+// repeat bit for bit.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fwi_precond.h"
+
+namespace {
+
+constexpr int kT = 256;                 // threads per block
+constexpr int kCB = 8;                  // channels per thread in the convolutions
+constexpr int kChunk = kT * 16;         // voxels per partial sum of the weight gradient
+constexpr int kTaps = 27;
+constexpr int64_t kMaxVox = int64_t(1) << 34;
+constexpr int kRedBlocks = 1024;
+
+__device__ __forceinline__ float bf2f(uint16_t u) { return __uint_as_float((unsigned)u << 16); }
+__device__ __forceinline__ uint16_t f2bf(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
+
+__global__ void __launch_bounds__(kT) conv_fwd_kernel(const uint16_t *__restrict__ x, const uint16_t *__restrict__ w,
+                                                      const float *__restrict__ b, int cin, int cout, int D, int H,
+                                                      int W, int relu, uint16_t *__restrict__ y) {
+  const int64_t nv = (int64_t)D * H * W;
+  const int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (p >= nv) return;
+  const int co0 = blockIdx.y * kCB;
+  const int nco = min(kCB, cout - co0);
+  const int px = (int)(p % W);
+  const int64_t r = p / W;
+  const int py = (int)(r % H), pz = (int)(r / H);
+  float acc[kCB];
+#pragma unroll
+  for (int c = 0; c < kCB; c++) acc[c] = (c < nco && b) ? b[co0 + c] : 0.f;
+  const int64_t wstride = (int64_t)cin * kTaps;  // between output channels
+  for (int ci = 0; ci < cin; ci++) {
+    const uint16_t *xc = x + (int64_t)ci * nv;
+    const uint16_t *wc = w + ((int64_t)co0 * cin + ci) * kTaps;
+    for (int kz = 0; kz < 3; kz++) {
+      const int z = pz + kz - 1;
+      if (z < 0 || z >= D) continue;
+      for (int ky = 0; ky < 3; ky++) {
+        const int yy = py + ky - 1;
+        if (yy < 0 || yy >= H) continue;
+        const uint16_t *row = xc + ((int64_t)z * H + yy) * W;
+        for (int kx = 0; kx < 3; kx++) {
+          const int xx = px + kx - 1;
+          if (xx < 0 || xx >= W) continue;
+          const float xv = bf2f(row[xx]);
+          const int t = (kz * 3 + ky) * 3 + kx;
+#pragma unroll
+          for (int c = 0; c < kCB; c++)
+            if (c < nco) acc[c] = fmaf(bf2f(wc[c * wstride + t]), xv, acc[c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kCB; c++)
+    if (c < nco) {
+      const float v = relu ? fmaxf(acc[c], 0.f) : acc[c];
+      y[(int64_t)(co0 + c) * nv + p] = f2bf(v);
+    }
+}
+
+// x at p feeds y at p + 1 - k along each axis (tap k), so dx[p] gathers dy there
+__global__ void __launch_bounds__(kT) conv_bwd_data_kernel(const float *__restrict__ dy,
+                                                           const uint16_t *__restrict__ w, int cin, int cout, int D,
+                                                           int H, int W, float *__restrict__ dx) {
+  const int64_t nv = (int64_t)D * H * W;
+  const int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x;
+  if (p >= nv) return;
+  const int ci0 = blockIdx.y * kCB;
+  const int nci = min(kCB, cin - ci0);
+  const int px = (int)(p % W);
+  const int64_t r = p / W;
+  const int py = (int)(r % H), pz = (int)(r / H);
+  float acc[kCB];
+#pragma unroll
+  for (int c = 0; c < kCB; c++) acc[c] = 0.f;
+  for (int co = 0; co < cout; co++) {
+    const float *dyc = dy + (int64_t)co * nv;
+    const uint16_t *wc = w + ((int64_t)co * cin + ci0) * kTaps;
+    for (int kz = 0; kz < 3; kz++) {
+      const int z = pz + 1 - kz;
+      if (z < 0 || z >= D) continue;
+      for (int ky = 0; ky < 3; ky++) {
+        const int yy = py + 1 - ky;
+        if (yy < 0 || yy >= H) continue;
+        const float *row = dyc + ((int64_t)z * H + yy) * W;
+        for (int kx = 0; kx < 3; kx++) {
+          const int xx = px + 1 - kx;
+          if (xx < 0 || xx >= W) continue;
+          const float dv = row[xx];
+          const int t = (kz * 3 + ky) * 3 + kx;
+#pragma unroll
+          for (int c = 0; c < kCB; c++)
+            if (c < nci) acc[c] = fmaf(bf2f(wc[c * kTaps + t]), dv, acc[c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kCB; c++)
+    if (c < nci) dx[(int64_t)(ci0 + c) * nv + p] = acc[c];
+}
+
+// partial sums over voxel chunk blockIdx.x of dy[co] x[ci](p + t - 1) (27 taps) and of
+// dy[co] (slot 27), for co = blockIdx.y, ci = blockIdx.z
+__global__ void __launch_bounds__(kT) conv_bwd_w_partial_kernel(const float *__restrict__ dy,
+                                                                const uint16_t *__restrict__ x, int cin, int cout,
+                                                                int D, int H, int W, float *__restrict__ part) {
+  __shared__ float red[kT / 32][kTaps + 1];
+  const int64_t nv = (int64_t)D * H * W;
+  const int64_t chunk = blockIdx.x;
+  const int co = blockIdx.y, ci = blockIdx.z;
+  const float *dyc = dy + (int64_t)co * nv;
+  const uint16_t *xc = x + (int64_t)ci * nv;
+  float acc[kTaps + 1];
+#pragma unroll
+  for (int t = 0; t <= kTaps; t++) acc[t] = 0.f;
+  const int64_t p1 = min(nv, (chunk + 1) * (int64_t)kChunk);
+  for (int64_t p = chunk * kChunk + threadIdx.x; p < p1; p += kT) {
+    const int px = (int)(p % W);
+    const int64_t r = p / W;
+    const int py = (int)(r % H), pz = (int)(r / H);
+    const float dv = dyc[p];
+    acc[kTaps] += dv;
+#pragma unroll
+    for (int kz = 0; kz < 3; kz++) {
+      const int z = pz + kz - 1;
+      const bool vz = z >= 0 && z < D;
+#pragma unroll
+      for (int ky = 0; ky < 3; ky++) {
+        const int yy = py + ky - 1;
+        const bool vy = vz && yy >= 0 && yy < H;
+#pragma unroll
+        for (int kx = 0; kx < 3; kx++) {
+          const int xx = px + kx - 1;
+          const int t = (kz * 3 + ky) * 3 + kx;
+          if (vy && xx >= 0 && xx < W) acc[t] = fmaf(dv, bf2f(xc[((int64_t)z * H + yy) * W + xx]), acc[t]);
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t <= kTaps; t++) {
+    float s = acc[t];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) red[warp][t] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x <= kTaps) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < kT / 32; q++) s += red[q][threadIdx.x];
+    part[((chunk * cout + co) * (int64_t)cin + ci) * (kTaps + 1) + threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kT) conv_bwd_w_sum_kernel(const float *__restrict__ part, int64_t nchunk, int cin,
+                                                            int cout, float *__restrict__ dw, float *__restrict__ db) {
+  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+  const int64_t npair = (int64_t)cout * cin;
+  if (i >= npair * (kTaps + 1)) return;
+  const int v = (int)(i % (kTaps + 1));
+  const int64_t pair = i / (kTaps + 1);  // co * cin + ci
+  float s = 0.f;
+  for (int64_t c = 0; c < nchunk; c++) s += part[(c * npair + pair) * (kTaps + 1) + v];
+  if (v < kTaps)
+    dw[pair * kTaps + v] = s;
+  else if (db && pair % cin == 0)
+    db[pair / cin] = s;
+}
+
+__global__ void __launch_bounds__(kT) relu_bwd_kernel(const float *__restrict__ dy, const uint16_t *__restrict__ y,
+                                                      int64_t n, float *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    out[i] = bf2f(y[i]) > 0.f ? dy[i] : 0.f;
+}
+
+__global__ void __launch_bounds__(kT) mse_partial_kernel(const uint16_t *__restrict__ y, const float *__restrict__ t,
+                                                         int64_t n, float inv_n, float *__restrict__ dy,
+                                                         double *__restrict__ part) {
+  __shared__ double sh[kT];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const float e = bf2f(y[i]) - t[i];
+    dy[i] = e * inv_n;
+    s += (double)e * (double)e;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void mse_final_kernel(const double *__restrict__ part, int nblocks, int64_t n, double *loss) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < nblocks; i++) s += part[i];
+  *loss = s / (2.0 * (double)n);
+}
+
+__global__ void __launch_bounds__(kT) adam_kernel(float *__restrict__ master, uint16_t *__restrict__ w,
+                                                  const float *__restrict__ g, float *__restrict__ m,
+                                                  float *__restrict__ v, int64_t n, float lr, float b1, float b2,
+                                                  float eps, float c1, float c2) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float p = master[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    master[i] = p;
+    if (w) w[i] = f2bf(p);
+  }
+}
+
+__global__ void __launch_bounds__(kT) to_bf16_kernel(const float *__restrict__ x, int64_t n, uint16_t *__restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) y[i] = f2bf(x[i]);
+}
+
+__global__ void __launch_bounds__(kT) from_bf16_kernel(const uint16_t *__restrict__ x, int64_t n, float *__restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) y[i] = bf2f(x[i]);
+}
+
+bool sizes_ok(int cin, int cout, int D, int H, int W) {
+  if (cin < 1 || cout < 1 || D < 1 || H < 1 || W < 1) return false;
+  if (cin > 65535 || cout > 65535) return false;  // grid y / z limits
+  return (int64_t)D * H * W <= kMaxVox;
+}
+
+unsigned grid_for(int64_t n) {
+  const int64_t b = (n + kT - 1) / kT;
+  return (unsigned)(b < 1 ? 1 : (b > 65536 ? 65536 : b));  // grid-stride loops cover the rest
+}
+
+fwi_status launched() { return cudaGetLastError() == cudaSuccess ? FWI_OK : FWI_E_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_nn_conv3d_forward(const uint16_t *x, const uint16_t *w, const float *b, int cin, int cout, int D,
+                                 int H, int W, int relu, uint16_t *y, void *stream) {
+  if (!x || !w || !y || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
+  const int64_t nv = (int64_t)D * H * W;
+  const dim3 grid((unsigned)((nv + kT - 1) / kT), (unsigned)((cout + kCB - 1) / kCB));
+  conv_fwd_kernel<<<grid, kT, 0, (cudaStream_t)stream>>>(x, w, b, cin, cout, D, H, W, relu, y);
+  return launched();
+}
+
+fwi_status fwi_nn_conv3d_backward_data(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
+                                       float *dx, void *stream) {
+  if (!dy || !w || !dx || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
+  const int64_t nv = (int64_t)D * H * W;
+  const dim3 grid((unsigned)((nv + kT - 1) / kT), (unsigned)((cin + kCB - 1) / kCB));
+  conv_bwd_data_kernel<<<grid, kT, 0, (cudaStream_t)stream>>>(dy, w, cin, cout, D, H, W, dx);
+  return launched();
+}
+
+int64_t fwi_nn_conv3d_backward_weight_work(int cin, int cout, int D, int H, int W) {
+  if (!sizes_ok(cin, cout, D, H, W)) return 0;
+  const int64_t nchunk = ((int64_t)D * H * W + kChunk - 1) / kChunk;
+  return nchunk * cout * (int64_t)cin * (kTaps + 1);
+}
+
+fwi_status fwi_nn_conv3d_backward_weight(const float *dy, const uint16_t *x, int cin, int cout, int D, int H, int W,
+                                         float *dw, float *db, float *work, void *stream) {
+  if (!dy || !x || !dw || !work || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
+  const int64_t nchunk = ((int64_t)D * H * W + kChunk - 1) / kChunk;
+  if (nchunk > 0x7fffffff) return FWI_E_INVAL;
+  const cudaStream_t s = (cudaStream_t)stream;
+  conv_bwd_w_partial_kernel<<<dim3((unsigned)nchunk, (unsigned)cout, (unsigned)cin), kT, 0, s>>>(dy, x, cin, cout, D,
+                                                                                                 H, W, work);
+  const int64_t nout = (int64_t)cout * cin * (kTaps + 1);
+  conv_bwd_w_sum_kernel<<<(unsigned)((nout + kT - 1) / kT), kT, 0, s>>>(work, nchunk, cin, cout, dw, db);
+  return launched();
+}
+
+fwi_status fwi_nn_relu_backward(const float *dy, const uint16_t *y, int64_t n, float *out, void *stream) {
+  if (!dy || !y || !out || n < 1) return FWI_E_INVAL;
+  relu_bwd_kernel<<<grid_for(n), kT, 0, (cudaStream_t)stream>>>(dy, y, n, out);
+  return launched();
+}
+
+fwi_status fwi_nn_mse(const uint16_t *y, const float *t, int64_t n, float *dy, double *loss, double *work,
+                      void *stream) {
+  if (!y || !t || !dy || !loss || !work || n < 1) return FWI_E_INVAL;
+  int64_t nb = (n + kT - 1) / kT;
+  if (nb > kRedBlocks) nb = kRedBlocks;
+  const cudaStream_t s = (cudaStream_t)stream;
+  mse_partial_kernel<<<(unsigned)nb, kT, 0, s>>>(y, t, n, (float)(1.0 / (double)n), dy, work);
+  mse_final_kernel<<<1, 32, 0, s>>>(work, (int)nb, n, loss);
+  return launched();
+}
+
+fwi_status fwi_nn_adam(float *master, uint16_t *w, const float *g, float *m, float *v, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int t, void *stream) {
+  if (!master || !g || !m || !v || n < 1 || t < 1 || !(beta1 >= 0.f && beta1 < 1.f) ||
+      !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) || !(lr > 0.f))
+    return FWI_E_INVAL;
+  // bias corrections 1 / (1 - beta^t), in FP64 on the host
+  double p1 = 1.0, p2 = 1.0;
+  for (int i = 0; i < t; i++) {
+    p1 *= beta1;
+    p2 *= beta2;
+  }
+  adam_kernel<<<grid_for(n), kT, 0, (cudaStream_t)stream>>>(master, w, g, m, v, n, lr, beta1, beta2, eps,
+                                                            (float)(1.0 / (1.0 - p1)), (float)(1.0 / (1.0 - p2)));
+  return launched();
+}
+
+fwi_status fwi_nn_to_bf16(const float *x, int64_t n, uint16_t *y, void *stream) {
+  if (!x || !y || n < 1) return FWI_E_INVAL;
+  to_bf16_kernel<<<grid_for(n), kT, 0, (cudaStream_t)stream>>>(x, n, y);
+  return launched();
+}
+
+fwi_status fwi_nn_from_bf16(const uint16_t *x, int64_t n, float *y, void *stream) {
+  if (!x || !y || n < 1) return FWI_E_INVAL;
+  from_bf16_kernel<<<grid_for(n), kT, 0, (cudaStream_t)stream>>>(x, n, y);
+  return launched();
+}
+
+}  // extern "C"

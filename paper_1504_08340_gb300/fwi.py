@@ -53,7 +53,11 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
            "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization",
-           "fwi_set_shot_batch", "fwi_tune_shot_batch")
+           "fwi_set_shot_batch", "fwi_tune_shot_batch",
+           # include/fwi_precond.h: the learned preconditioner's kernels
+           "fwi_nn_conv3d_forward", "fwi_nn_conv3d_backward_data", "fwi_nn_conv3d_backward_weight_work",
+           "fwi_nn_conv3d_backward_weight", "fwi_nn_relu_backward", "fwi_nn_mse", "fwi_nn_adam", "fwi_nn_to_bf16",
+           "fwi_nn_from_bf16")
 
 _lib = None
 
@@ -96,9 +100,20 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_set_shot_batch.argtypes = [P, I]
     lib.fwi_tune_shot_batch.argtypes = [P, I, I, I, I, C.c_double, C.POINTER(I)]
     lib.fwi_regularization.argtypes = [P, I, C.c_double, D, P, P, I]
+    L, Fl = C.c_int64, C.c_float
+    lib.fwi_nn_conv3d_forward.argtypes = [P, P, P, I, I, I, I, I, I, P, P]
+    lib.fwi_nn_conv3d_backward_data.argtypes = [P, P, I, I, I, I, I, P, P]
+    lib.fwi_nn_conv3d_backward_weight_work.argtypes = [I, I, I, I, I]
+    lib.fwi_nn_conv3d_backward_weight.argtypes = [P, P, I, I, I, I, I, P, P, P, P]
+    lib.fwi_nn_relu_backward.argtypes = [P, P, L, P, P]
+    lib.fwi_nn_mse.argtypes = [P, P, L, P, P, P, P]
+    lib.fwi_nn_adam.argtypes = [P, P, P, P, P, L, Fl, Fl, Fl, Fl, I, P]
+    lib.fwi_nn_to_bf16.argtypes = [P, L, P, P]
+    lib.fwi_nn_from_bf16.argtypes = [P, L, P, P]
     for name in EXPORTS:
         if name not in ("fwi_destroy", "fwi_last_error", "fwi_status_string"):
             getattr(lib, name).restype = I
+    lib.fwi_nn_conv3d_backward_weight_work.restype = L
     _lib = lib
     return lib
 

@@ -7,9 +7,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "fwi.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fwi_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fwi_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol():
@@ -89,4 +93,18 @@ def test_null_context_is_rejected_without_touching_the_gpu():
     # argument checks of the allocation-free misfit come before any device work too
     assert lib.fwi_trace_misfit_noalloc(nul, nul, 10, 4, 1e-3, nul, nul) == inval
     assert set(calls) | {"fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string",
-                         "fwi_trace_misfit_noalloc"} == set(fwi.EXPORTS)
+                         "fwi_trace_misfit_noalloc"} == {e for e in fwi.EXPORTS if not e.startswith("fwi_nn_")}
+    # the preconditioner kernels check pointers and sizes before any device work
+    one = C.c_void_p(1)
+    assert lib.fwi_nn_conv3d_forward(nul, one, nul, 1, 1, 2, 2, 2, 0, one, nul) == inval
+    assert lib.fwi_nn_conv3d_forward(one, one, nul, 0, 1, 2, 2, 2, 0, one, nul) == inval
+    assert lib.fwi_nn_conv3d_backward_data(one, one, 1, 1, 0, 2, 2, one, nul) == inval
+    assert lib.fwi_nn_conv3d_backward_weight(one, one, 1, 1, 2, 2, 2, one, nul, nul, nul) == inval
+    assert lib.fwi_nn_conv3d_backward_weight_work(0, 1, 2, 2, 2) == 0
+    assert lib.fwi_nn_conv3d_backward_weight_work(3, 4, 2, 2, 2) == 1 * 4 * 3 * 28
+    assert lib.fwi_nn_relu_backward(one, one, 0, one, nul) == inval
+    assert lib.fwi_nn_mse(one, one, 10, one, nul, one, nul) == inval
+    assert lib.fwi_nn_adam(one, nul, one, one, one, 10, 1e-3, 0.9, 0.999, 1e-8, 0, nul) == inval
+    assert lib.fwi_nn_adam(one, nul, one, one, one, 10, 1e-3, 1.0, 0.999, 1e-8, 1, nul) == inval
+    assert lib.fwi_nn_to_bf16(nul, 4, one, nul) == inval
+    assert lib.fwi_nn_from_bf16(one, 4, nul, nul) == inval
