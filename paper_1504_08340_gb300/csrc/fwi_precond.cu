@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "fwi_precond.h"
 
 namespace {
@@ -316,11 +318,7 @@ fwi_status fwi_nn_adam(float *master, uint16_t *w, const float *g, float *m, flo
       !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) || !(lr > 0.f))
     return FWI_E_INVAL;
   // bias corrections 1 / (1 - beta^t), in FP64 on the host
-  double p1 = 1.0, p2 = 1.0;
-  for (int i = 0; i < t; i++) {
-    p1 *= beta1;
-    p2 *= beta2;
-  }
+  const double p1 = std::pow((double)beta1, t), p2 = std::pow((double)beta2, t);
   adam_kernel<<<grid_for(n), kT, 0, (cudaStream_t)stream>>>(master, w, g, m, v, n, lr, beta1, beta2, eps,
                                                             (float)(1.0 / (1.0 - p1)), (float)(1.0 / (1.0 - p2)));
   return launched();
