@@ -7,7 +7,8 @@ FP64 gradients are summed once per evaluation. That sum is the only exchange.
 
 The sum is formed in a fixed rank order (all-gather, then rank 0 + rank 1 + ...), so
 every rank holds the same bits whatever reduction tree the backend would use. The
-collective runs on the tensors' device: NCCL for CUDA tensors, gloo for CPU ones.
+collectives run on the default process group (or the one passed in) with tensors on
+the gradients' device: an NCCL group for CUDA tensors, a gloo group for CPU ones.
 """
 from __future__ import annotations
 
