@@ -295,11 +295,13 @@ fwi_status fwi_reset_timing(fwi_ctx *ctx);
  * traces, observed: device arrays of (nsteps+1)*nrec*3 floats ([n][r][c]);
  * J: host. The call allocates nothing: its scratch is a fixed 512 KiB device
  * array inside the library, which every GPU that loads the library keeps until
- * the process exits. The first call on a device looks up that array's address
- * (do it before any stream capture). Calls share the array, so calls that
- * overlap on the GPU race. Errors: FWI_E_INVAL (null pointers, nrec < 1,
- * dt <= 0, or nsteps + 1 > 65536, the scratch limit), FWI_E_NONFINITE (a trace
- * value is NaN/Inf), FWI_E_CUDA. */
+ * the process exits. Each call looks up that array's address in the current
+ * context. The call is synchronous (it waits on cuda_stream before returning),
+ * so it must not be issued on a stream that is being captured. Calls share the
+ * array, so calls that overlap on the GPU race. Errors: FWI_E_INVAL (null
+ * pointers, nrec < 1, dt <= 0, or nsteps + 1 > 65536, the scratch limit),
+ * FWI_E_NONFINITE (a trace or observed value is NaN/Inf, or the sum overflows),
+ * FWI_E_CUDA. */
 fwi_status fwi_trace_misfit_noalloc(const float *traces, const float *observed, int nsteps, int nrec,
                                     double dt, void *cuda_stream, double *J);
 

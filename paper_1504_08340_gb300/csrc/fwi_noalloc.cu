@@ -10,7 +10,7 @@
 // cudaMalloc. The caller passes inputs and outputs; the call allocates nothing.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <cmath>
 
 #include "../../include/fwi.h"
 
@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(kThreads) sample_sums(const float *tr, const f
     bool bad = false;
     for (int64_t i = threadIdx.x; i < per_sample; i += kThreads) {
       const float t = tr[(int64_t)n * per_sample + i];
-      if (!isfinite(t)) bad = true;
-      const float e = t - ob[(int64_t)n * per_sample + i];  // as fwi_misfit: FP32 residual, FP64 sum
+      const float o = ob[(int64_t)n * per_sample + i];
+      if (!isfinite(t) || !isfinite(o)) bad = true;
+      const float e = t - o;  // as fwi_misfit: FP32 residual, FP64 sum
       acc += (double)e * (double)e;
     }
     if (bad) *flag = 1.0;
@@ -68,25 +69,16 @@ __global__ void __launch_bounds__(kThreads) trapezoid_total(const double *part, 
   if (threadIdx.x == 0) *out = 0.5 * dt * sh[0];
 }
 
-// Device address of the scratch array, looked up once per device. In host code
-// the name g_misfit_scratch is only a host-side stand-in, not a device address.
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double *g_scratch_ptr[kMaxDevices] = {};
-
+// Device address of the scratch array in the current context. In host code the
+// name g_misfit_scratch is only a host-side stand-in, not a device address, so
+// every call asks the runtime for the address in the context that is current
+// now. The lookup is a cheap host call; not caching it means a context that was
+// torn down and created again never sees a stale address.
 cudaError_t scratch_for_current_device(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_misfit_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_misfit_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double *>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double *>(p);
   return cudaSuccess;
 }
 
@@ -95,7 +87,7 @@ cudaError_t scratch_for_current_device(double **out) {
 extern "C" fwi_status fwi_trace_misfit_noalloc(const float *traces, const float *observed, int nsteps, int nrec,
                                                double dt, void *cuda_stream, double *J) {
   if (!traces || !observed || !J || nrec < 1 || nsteps < 0 || !(dt > 0)) return FWI_E_INVAL;
-  if (nsteps + 1 > kMaxSamples) return FWI_E_INVAL;  // more time samples than the scratch holds
+  if (nsteps >= kMaxSamples) return FWI_E_INVAL;  // more time samples than the scratch holds
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double *scratch = nullptr;
   if (scratch_for_current_device(&scratch) != cudaSuccess) return FWI_E_CUDA;
@@ -110,7 +102,7 @@ extern "C" fwi_status fwi_trace_misfit_noalloc(const float *traces, const float 
   double host[2] = {0.0, 0.0};
   if (cudaMemcpyAsync(host, total, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FWI_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return FWI_E_CUDA;
-  if (host[1] != 0.0) return FWI_E_NONFINITE;
+  if (host[1] != 0.0 || !std::isfinite(host[0])) return FWI_E_NONFINITE;
   *J = host[0];
   return FWI_OK;
 }

@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 def test_noalloc_misfit_matches_fwi_misfit():
     torch = pytest.importorskip("torch")
     from paper_1504_08340_gb300 import Context, load_library
+    from paper_1504_08340_gb300.fwi import FWIError
 
     lib = load_library()
     fn = lib.fwi_trace_misfit_noalloc
@@ -50,3 +51,27 @@ def test_noalloc_misfit_matches_fwi_misfit():
         st = fn(ctypes.c_void_p(traces.data_ptr()), ctypes.c_void_p(obs.data_ptr()), 70000, ctx.nrec, w.dt,
                 ctypes.c_void_p(stream), ctypes.byref(J))
         assert st == 1 and J.value == -1.0
+        # a NaN in either input is reported as FWI_E_NONFINITE, J untouched; fwi_misfit agrees
+        for which in ("traces", "observed"):
+            bad_t, bad_o = traces.clone(), obs.clone()
+            (bad_t if which == "traces" else bad_o)[0, w.nsteps // 2, 0, 1] = float("nan")
+            J = ctypes.c_double(-1.0)
+            st = fn(ctypes.c_void_p(bad_t.data_ptr()), ctypes.c_void_p(bad_o.data_ptr()), w.nsteps, ctx.nrec,
+                    w.dt, ctypes.c_void_p(stream), ctypes.byref(J))
+            assert st == 5 and J.value == -1.0, (which, st)
+            if which == "observed":
+                with pytest.raises(FWIError) as err:
+                    ctx.misfit(bad_o)
+                assert err.value.code == 5
+        # the flag of the failed call does not leak into the next one
+        J = ctypes.c_double()
+        st = fn(ctypes.c_void_p(traces.data_ptr()), ctypes.c_void_p(obs.data_ptr()), w.nsteps, ctx.nrec, w.dt,
+                ctypes.c_void_p(stream), ctypes.byref(J))
+        assert st == 0 and abs(J.value - ctx.misfit(obs)) <= 1e-12 * J.value
+        # nsteps = 0: one sample with trapezoid weight 1/2
+        e = (traces[0, 0].double() - obs[0, 0].double()).cpu().numpy()
+        J = ctypes.c_double()
+        st = fn(ctypes.c_void_p(traces.data_ptr()), ctypes.c_void_p(obs.data_ptr()), 0, ctx.nrec, w.dt,
+                ctypes.c_void_p(stream), ctypes.byref(J))
+        expect = 0.5 * w.dt * 0.5 * float((e * e).sum())
+        assert st == 0 and abs(J.value - expect) <= 1e-12 * max(expect, 1e-300), (J.value, expect)
