@@ -55,7 +55,11 @@
  * Pins: see tests/test_oracle_*.py (stiffness symmetry and rigid modes, patch
  * test, transposes by the dot-product test, RK4 against the exact amplification
  * of an eigenmode, energy, state counts printed in Sec. 4.2 / 4.5, directional
- * finite differences as in Sec. 4.1 / Table 2).
+ * finite differences as in Sec. 4.1 / Table 2; the PML coupling operators and
+ * lumped a, b, c, d against the stretched-coordinate stress and divergence in the
+ * Laplace domain, the identity-stretch patch test across the interface, the
+ * wavelet's closed forms, trivial forward cases, PML reflection against a wider
+ * domain, and Stokes' point-force solution in a homogeneous full space).
  * Parity unpinned: the absolute values of Table 2 (trial model, PML details
  * of [13] and the data mesh are not given in the paper).
  *
