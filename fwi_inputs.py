@@ -178,6 +178,10 @@ def grf_64x64x32():  # single shot, smooth Gaussian random field, 2000 steps, 32
     return build(Workload("grf_64x64x32", 64, 64, 32, 10, 1.0, 2000, 10.0, 32, seed=2))
 
 
+def grf_16x16x8():  # the single-shot recipe (GRF, 10-element PML, f0, dt, 2000 steps) on a 16x16x8 box
+    return build(Workload("grf_16x16x8", 16, 16, 8, 10, 1.0, 2000, 10.0, 8, seed=2))
+
+
 def layered_96x96x48():  # 3 layers + sharp inclusion, 16 shots, 3000 steps, 48x48 receivers
     return build(Workload("layered_96x96x48", 96, 96, 48, 10, 1.0, 3000, 10.0, 48, nshots=16, seed=3))
 

@@ -279,6 +279,14 @@ fwi_status fwi_get_mass_tilde(fwi_ctx *ctx, double *mtilde);
  * fields zero off the PML nodes. Errors: FWI_E_STATE (no material). */
 fwi_status fwi_rhs(fwi_ctx *ctx, int adjoint, const float *state, float *rate, int on_device);
 
+/* The RK4 state at the end of the most recent sweep, in the layout of fwi_rhs
+ * (27 fields of dims[5] floats, host or device): after fwi_forward(ctx, s, 1, ...)
+ * it is shot s's state x(t_N) of (6) (displacement, rate and history levels, the
+ * PML stresses). A diagnostic accessor, e.g. for energy checks; after a gradient
+ * evaluation it holds the adjoint state instead. Caller-owned output; synchronous.
+ * Errors: FWI_E_INVAL (null), FWI_E_STATE (no state buffers), FWI_E_CUDA. */
+fwi_status fwi_get_state(fwi_ctx *ctx, float *state, int on_device);
+
 /* Kernel timing: with enable = 1 every stage-kernel launch of later calls is
  * bracketed by CUDA events on the context's stream; fwi_get_timing returns the
  * summed device time (ms) and launch count of kernel class `which`

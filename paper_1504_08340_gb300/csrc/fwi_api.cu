@@ -1271,6 +1271,18 @@ fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int
   return FWI_OK;
 }
 
+fwi_status fwi_get_state(fwi_ctx *c, float *state, int on_device) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (!state) return fail(c, FWI_E_INVAL, "null argument");
+  if (!c->state[0]) return fail(c, FWI_E_STATE, "no RK4 state buffers (a shot batch allocation failed)");
+  const size_t n = set_floats(c);
+  CUDA_TRY(c, cudaMemcpyAsync(state, c->state[0], n * sizeof(float),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
 fwi_status fwi_regularization(fwi_ctx *c, int kind, double eps, double *R, double *g_lambda, double *g_mu,
                               int on_device) {
   if (!c) return FWI_E_INVAL;

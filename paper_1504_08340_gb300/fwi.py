@@ -50,7 +50,7 @@ class StepInfo(C.Structure):
 # every symbol the header declares; the CPU test checks the library exports them all
 EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_get_dims",
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
-           "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_set_timing",
+           "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_get_state", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
            "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization",
            "fwi_set_shot_batch", "fwi_tune_shot_batch",
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_adjoint_gradient.argtypes = [P, I, I, P, I, D, P, P]
     lib.fwi_get_mass_tilde.argtypes = [P, D]
     lib.fwi_rhs.argtypes = [P, I, P, P, I]
+    lib.fwi_get_state.argtypes = [P, P, I]
     lib.fwi_set_timing.argtypes = [P, I]
     lib.fwi_get_timing.argtypes = [P, I, D, I64]
     lib.fwi_reset_timing.argtypes = [P]
@@ -287,6 +288,14 @@ class Context:
         if ds != do:
             raise TypeError("state and rate must both be host or both be device arrays")
         self._check(self.lib.fwi_rhs(self.ptr, int(adjoint), ps, po, ds))
+        return out
+
+    def state(self, out=None):
+        """The RK4 state at the end of the last sweep ([27, stride] float32; fwi_get_state)."""
+        if out is None:
+            out = np.zeros((27, self.stride), dtype=np.float32)
+        p, dev = _ptr(out, np.float32)
+        self._check(self.lib.fwi_get_state(self.ptr, p, dev))
         return out
 
     def regularization(self, kind="tn", eps=0.0, device=False):

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import fwi_inputs as fi
-from helpers import rel_l2
+from helpers import node_classes, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -98,13 +98,24 @@ def test_rhs_parity(oracle_mod, mesh, adjoint):
         D = np.ones(9)
         D[3:] = -1
         ref = np.stack([ref[0] * D, -ref[1] * D, ref[2] * D])
-    for l in range(3):
-        for sl, name in ((slice(0, 3), "u"), (slice(3, 9), "S")):
-            r = ref[l][:, sl]
-            if np.abs(r).max() == 0:
-                assert np.abs(out[l][:, sl]).max() == 0
-                continue
-            assert rel_l2(out[l][:, sl], r) < 2e-5, (l, name, rel_l2(out[l][:, sl], r))
+    _check_by_class(o, out, ref)
+
+
+def _check_by_class(o, out, ref, tol=2e-5):
+    """Relative L2 per level, field group (u, S) and node set (interior, shell, outer-face
+    PML, deep PML), so that an error confined to a small node set is not diluted by the
+    others; an all-zero reference block must come out exactly zero."""
+    for cls, mask in node_classes(o).items():
+        if not mask.any():
+            continue
+        for l in range(3):
+            for sl, name in ((slice(0, 3), "u"), (slice(3, 9), "S")):
+                r = ref[l][mask][:, sl]
+                g = out[l][mask][:, sl]
+                if np.abs(r).max() == 0:
+                    assert np.abs(g).max() == 0, (cls, l, name)
+                    continue
+                assert rel_l2(g, r) < tol, (cls, l, name, rel_l2(g, r))
 
 
 def test_dims_and_pml_node_count(oracle_mod):
@@ -205,9 +216,7 @@ def test_grf_64x64x32_full_size_sampled(oracle_mod):
     with _ctx(w) as ctx:
         ctx.set_material(lam, mu)
         out = from_gpu_layout(ctx.rhs(to_gpu_layout(Y, ctx)), ctx)
-    for l in range(3):
-        for sl in (slice(0, 3), slice(3, 9)):
-            assert rel_l2(out[l][:, sl], ref[l][:, sl]) < 2e-5
+    _check_by_class(o, out, ref)
     del o
     w.nsteps = 4
     _check_gradient(oracle_mod, w, wparams=(w.f0, 0.0, 1e3))

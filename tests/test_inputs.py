@@ -17,6 +17,7 @@ def _velocities(w, which):
     (fi.box_8x8x4, (8, 8, 4, 3), 300, 15.0, 25, 1, 12_615, 2_601),
     (fi.grf_64x64x32, (64, 64, 32, 10), 2000, 10.0, 1024, 1, 2_427_685, 1_081_665),
     (fi.layered_96x96x48, (96, 96, 48, 10), 3000, 10.0, 2304, 16, 6_351_813, 3_613_153),
+    (fi.grf_16x16x8, (16, 16, 8, 10), 2000, 10.0, 64, 1, 197_173, 18_513),
 ])
 def test_workload_sizes(make, mesh, steps, f0, nrec, nshots, nodes, mat_nodes):
     w = make()
