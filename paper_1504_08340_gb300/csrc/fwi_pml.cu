@@ -514,6 +514,19 @@ constexpr int kBX = 32, kBY = FWI_PML_BY;
 
 // grid.x: blocks of kBY warp tasks (see Region); tasks of a box run plane by plane.
 // The boxes exclude the outer faces of the grid, so every node takes the bulk path.
+// PART 3 runs the stress-row update and then the displacement-row update of the same
+// pair in the same thread: each part keeps its own register footprint, and the second
+// part's loads (the rows the first part just read) hit in L1/L2 instead of DRAM.
+template <bool ADJ, int MODE, int KY, int KZ, int PART>
+__device__ __forceinline__ void pml_task(const Geo &g, const StageArgs &a, int I0, int J, int K, bool even_ok) {
+  if constexpr (PART == 3) {
+    pml_pair<ADJ, MODE, KY, KZ, 1>(g, a, I0, J, K, even_ok);
+    pml_pair<ADJ, MODE, KY, KZ, 2>(g, a, I0, J, K, even_ok);
+  } else {
+    pml_pair<ADJ, MODE, KY, KZ, PART>(g, a, I0, J, K, even_ok);
+  }
+}
+
 template <bool ADJ, int MODE, int PART>
 __global__ void __launch_bounds__(kBX *kBY, PART == 0 ? FWI_PML_MINB : FWI_PML_SPLIT_MINB)
     pml_kernel(Geo g, StageArgs a0, Region r) {
@@ -546,11 +559,11 @@ __global__ void __launch_bounds__(kBX *kBY, PART == 0 ? FWI_PML_MINB : FWI_PML_S
     // the even node of a box's first pair may not be (its results are dropped)
     const bool even_ok = I0 >= r.lo[b][0];
     if (ky == kSC) {
-      if (kz == kSC) pml_pair<ADJ, MODE, kSC, kSC, PART>(g, a, I0, J, K, even_ok);
-      else pml_pair<ADJ, MODE, kSC, kSLR, PART>(g, a, I0, J, K, even_ok);
+      if (kz == kSC) pml_task<ADJ, MODE, kSC, kSC, PART>(g, a, I0, J, K, even_ok);
+      else pml_task<ADJ, MODE, kSC, kSLR, PART>(g, a, I0, J, K, even_ok);
     } else {
-      if (kz == kSC) pml_pair<ADJ, MODE, kSLR, kSC, PART>(g, a, I0, J, K, even_ok);
-      else pml_pair<ADJ, MODE, kSLR, kSLR, PART>(g, a, I0, J, K, even_ok);
+      if (kz == kSC) pml_task<ADJ, MODE, kSLR, kSC, PART>(g, a, I0, J, K, even_ok);
+      else pml_task<ADJ, MODE, kSLR, kSLR, PART>(g, a, I0, J, K, even_ok);
     }
   }
 }
@@ -643,11 +656,10 @@ int launch_pml(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
       else pml_kernel<false, 3, P><<<grd, blk, 0, st>>>(g, a, r);
     }
   };
-  // two launches: the stress rows, then the displacement rows (disjoint outputs, the same
-  // inputs). Each needs fewer registers than the whole update, so more warps are resident.
-  go(std::integral_constant<int, 1>{}, s);
-  go(std::integral_constant<int, 2>{}, s);
-  return 2;
+  // one launch: per pair the stress rows, then the displacement rows (disjoint outputs, the
+  // same inputs), each part with the registers of its own update
+  go(std::integral_constant<int, 3>{}, s);
+  return 1;
 }
 
 int launch_pml_face(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
