@@ -287,6 +287,17 @@ fwi_status fwi_rhs(fwi_ctx *ctx, int adjoint, const float *state, float *rate, i
  * Errors: FWI_E_INVAL (null), FWI_E_STATE (no state buffers), FWI_E_CUDA. */
 fwi_status fwi_get_state(fwi_ctx *ctx, float *state, int on_device);
 
+/* CUDA graphs for the time loops: with enable = 1, each sweep of a later call (a forward
+ * sweep, the adjoint sweep over the stored history, one checkpoint segment) is recorded by
+ * stream capture the first time it runs with a given shot group and replayed as one
+ * graph launch afterwards. A replay issues the same kernels with the same arguments in
+ * the same order as the direct launches, so results are bitwise the same; it saves the
+ * host launch work and the gaps between kernels. Recorded graphs are dropped when any
+ * device buffer of the library is allocated or freed (they hold raw pointers), when
+ * graphs are turned off, and at fwi_destroy. Kernel timing (fwi_set_timing) runs the
+ * sweeps directly. Not in the paper. Errors: FWI_E_INVAL, FWI_E_CUDA. */
+fwi_status fwi_set_graphs(fwi_ctx *ctx, int enable);
+
 /* Kernel timing: with enable = 1 every stage-kernel launch of later calls is
  * bracketed by CUDA events on the context's stream; fwi_get_timing returns the
  * summed device time (ms) and launch count of kernel class `which`

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,6 +25,7 @@ struct fwi_ctx {
   fwi::Geo geo{};
   cudaStream_t stream = nullptr;
   cudaStream_t side[2] = {nullptr, nullptr};  // the stage's kernels fork onto these and join back
+  cudaStream_t cap = nullptr;  // sweeps are recorded on this stream (the caller's may be the legacy one)
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   bool cuda_failed = false;
   std::string err;
@@ -79,6 +81,19 @@ struct fwi_ctx {
   // regularisation (fwi_regularization): gradients, block partials, functional values
   double *d_rg = nullptr, *d_rpart = nullptr, *d_rval = nullptr;
 
+  // recorded sweeps (fwi_set_graphs): kind 0 forward sweep, 1 adjoint sweep over the stored
+  // history, 2 one checkpoint segment (recompute and adjoint); a, b, g identify the shots
+  // and the segment
+  struct Graph {
+    int kind, a, b, g;
+    const float *st;
+    uint64_t gen;
+    cudaGraphExec_t exec;
+    int64_t launches[4];
+  };
+  bool graphs = false;
+  std::vector<Graph> gcache;
+
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
@@ -116,9 +131,14 @@ fwi_status fail(fwi_ctx *c, fwi_status s, const char *fmt, ...) {
     if (s_ != FWI_OK) return s_;      \
   } while (0)
 
+// bumped by every device allocation and free: a recorded CUDA graph holds raw pointers, so
+// a cached graph is replayed only while no buffer has changed since it was recorded
+std::atomic<uint64_t> g_alloc_gen{0};
+
 template <class T>
 fwi_status dalloc(fwi_ctx *c, T **p, size_t n) {
   if (*p) return FWI_OK;
+  g_alloc_gen++;
   cudaError_t e = cudaMalloc((void **)p, n * sizeof(T) + 16);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -130,7 +150,10 @@ fwi_status dalloc(fwi_ctx *c, T **p, size_t n) {
 
 template <class T>
 void dfree(T *&p) {
-  if (p) cudaFree((void *)p);
+  if (p) {
+    g_alloc_gen++;
+    cudaFree((void *)p);
+  }
   p = nullptr;
 }
 
@@ -164,6 +187,58 @@ double mass_u(const fwi_ctx *c, int i, int j, int k) {
 
 fwi_status check_stream(fwi_ctx *c) {
   if (c->cuda_failed) return fail(c, FWI_E_CUDA, "context unusable after an earlier CUDA error: %s", c->err.c_str());
+  return FWI_OK;
+}
+
+void drop_graphs(fwi_ctx *c) {
+  for (auto &e : c->gcache) cudaGraphExecDestroy(e.exec);
+  c->gcache.clear();
+}
+
+// Runs body() (stream work on the context's stream and its side streams) directly, or, with
+// graphs on (and kernel timing off), replays it as a CUDA graph: the first call with a
+// given key records body() by stream capture; later calls with the same key and no device
+// allocation in between launch the recorded graph, which issues the same kernels with the
+// same arguments in the same order.
+template <class F>
+fwi_status graphed(fwi_ctx *c, int kind, int a, int b, int g, F body) {
+  if (!c->graphs || c->timing) return body();
+  const uint64_t gen = g_alloc_gen.load();
+  for (const auto &e : c->gcache)
+    if (e.gen != gen) {
+      drop_graphs(c);
+      break;
+    }
+  for (const auto &e : c->gcache)
+    if (e.kind == kind && e.a == a && e.b == b && e.g == g && e.st == c->state[0]) {
+      CUDA_TRY(c, cudaGraphLaunch(e.exec, c->stream));
+      for (int i = 0; i < 4; i++) c->t_launch[i] += e.launches[i];
+      return FWI_OK;
+    }
+  if (c->gcache.size() >= 512) drop_graphs(c);
+  int64_t before[4];
+  for (int i = 0; i < 4; i++) before[i] = c->t_launch[i];
+  // record on the library's own stream (nothing runs while recording); the graph is then
+  // launched on the context's stream, after the work already queued there
+  const cudaStream_t user = c->stream;
+  CUDA_TRY(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap;
+  const fwi_status st = body();
+  c->stream = user;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(c->cap, &graph);
+  if (st != FWI_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ee != cudaSuccess) return fail(c, FWI_E_CUDA, "stream capture of a sweep failed: %s", cudaGetErrorString(ee));
+  fwi_ctx::Graph e{kind, a, b, g, c->state[0], gen, nullptr, {0, 0, 0, 0}};
+  const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return fail(c, FWI_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+  for (int i = 0; i < 4; i++) e.launches[i] = c->t_launch[i] - before[i];
+  c->gcache.push_back(e);
+  CUDA_TRY(c, cudaGraphLaunch(e.exec, c->stream));
   return FWI_OK;
 }
 
@@ -328,8 +403,8 @@ fwi_status ensure_trace_buffers(fwi_ctx *c) {
 // forward sweep of shots shot0 .. shot0 + nb - 1 into d_traces (shot b at b * trace_floats);
 // hist: optional displacement history (shot b at b * hstride); snap: optional snapshots of
 // the step-start state X every `every` steps (shot b's segment g at (b * nseg + g) * set)
-fwi_status forward_sweep(fwi_ctx *c, int shot0, int nb, float *hist, int64_t hstride, float *snap = nullptr,
-                         int every = 0, int nseg = 0) {
+fwi_status forward_sweep_body(fwi_ctx *c, int shot0, int nb, float *hist, int64_t hstride, float *snap, int every,
+                              int nseg) {
   TRY(zero_state(c));
   const int64_t per_step = (int64_t)c->nrec * 3;
   const size_t hstep = level_floats(c);
@@ -353,6 +428,13 @@ fwi_status forward_sweep(fwi_ctx *c, int shot0, int nb, float *hist, int64_t hst
   }
   CUDA_TRY(c, cudaGetLastError());
   return FWI_OK;
+}
+
+fwi_status forward_sweep(fwi_ctx *c, int shot0, int nb, float *hist, int64_t hstride, float *snap = nullptr,
+                         int every = 0, int nseg = 0) {
+  // hist, snap and their strides follow from the context's buffers and checkpointing mode
+  return graphed(c, 0, shot0, nb, hist ? 1 : (snap ? 2 + every : 0),
+                 [&] { return forward_sweep_body(c, shot0, nb, hist, hstride, snap, every, nseg); });
 }
 
 // residual and misfit of the traces of batch shot b against observed (device) -> d_J[slot]
@@ -515,6 +597,8 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
       st = fail(c, FWI_E_CUDA, "stream setup failed");
   if (st == FWI_OK && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
     st = fail(c, FWI_E_CUDA, "event setup failed");
+  if (st == FWI_OK && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+    st = fail(c, FWI_E_CUDA, "stream setup failed");
   const size_t sbytes = (size_t)fwi::kFields * g.stride;
   for (int b = 0; b < 4 && st == FWI_OK; b++) st = dalloc(c, &c->state[b], sbytes);
   for (int ax = 0; ax < 3 && st == FWI_OK; ax++) {
@@ -616,6 +700,7 @@ void fwi_destroy(fwi_ctx *c) {
   dfree(c->d_mu);
   dfree(c->d_lam_n);
   dfree(c->d_mu_n);
+  drop_graphs(c);
   dfree(c->d_shell);
   dfree(c->d_face);
   dfree(c->d_wave);
@@ -645,6 +730,7 @@ void fwi_destroy(fwi_ctx *c) {
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->cap) cudaStreamDestroy(c->cap);
   for (auto e : c->ev_free) cudaEventDestroy(e);
   for (auto &p : c->ev_pending) {
     cudaEventDestroy(p.first);
@@ -901,30 +987,38 @@ fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed
       TRY(misfit_of_traces(c, b, obs, s0 + b));
     }
     // adjoint sweep in reversed time with the gradient time integral (C.1f)/(C.1g)
-    TRY(zero_state(c));
     if (every == 0) {
-      for (int lvl = N - 1; lvl >= 0; lvl--) TRY(adjoint_level(c, lvl, c->d_hist + (size_t)lvl * hstep, nb, hstride));
+      TRY(graphed(c, 1, 0, nb, 0, [&]() -> fwi_status {
+        TRY(zero_state(c));
+        for (int lvl = N - 1; lvl >= 0; lvl--)
+          TRY(adjoint_level(c, lvl, c->d_hist + (size_t)lvl * hstep, nb, hstride));
+        return FWI_OK;
+      }));
       continue;
     }
+    TRY(zero_state(c));
     // checkpointed: segment g holds the steps [g every, min((g+1) every, N)). Its forward
     // steps are recomputed from snapshot g in the second state set, writing the history
     // levels g every + 1 .. of the segment; then the adjoint runs through those levels.
     // The recomputed steps repeat the forward sweep's arithmetic exactly, so the
     // gradient equals the one from the stored history bit for bit.
     for (int g = nseg - 1; g >= 0; g--) {
-      const int L0 = g * every, L1 = std::min(L0 + every, N);
-      std::swap(c->state, c->rstate);
-      fwi_status rs = FWI_OK;
-      for (int b = 0; b < nb && rs == FWI_OK; b++)
-        if (cudaMemcpyAsync(c->state[0] + b * sfloats, c->d_snap + ((size_t)b * nseg + g) * sfloats,
-                            sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-          rs = fail(c, FWI_E_CUDA, "snapshot restore failed");
-      for (int n = L0; n < L1 && rs == FWI_OK; n++)
-        rs = rk4_step(c, false, n, shot0 + s0, nb, c->d_hist + (size_t)(n + 1 - L0) * hstep, hstride);
-      std::swap(c->state, c->rstate);
-      TRY(rs);
-      for (int lvl = std::min(L1, N - 1); lvl > L0; lvl--)
-        TRY(adjoint_level(c, lvl, c->d_hist + (size_t)(lvl - L0) * hstep, nb, hstride));
+      TRY(graphed(c, 2, shot0 + s0, nb, g * 65536 + every, [&]() -> fwi_status {
+        const int L0 = g * every, L1 = std::min(L0 + every, N);
+        std::swap(c->state, c->rstate);
+        fwi_status rs = FWI_OK;
+        for (int b = 0; b < nb && rs == FWI_OK; b++)
+          if (cudaMemcpyAsync(c->state[0] + b * sfloats, c->d_snap + ((size_t)b * nseg + g) * sfloats,
+                              sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            rs = fail(c, FWI_E_CUDA, "snapshot restore failed");
+        for (int n = L0; n < L1 && rs == FWI_OK; n++)
+          rs = rk4_step(c, false, n, shot0 + s0, nb, c->d_hist + (size_t)(n + 1 - L0) * hstep, hstride);
+        std::swap(c->state, c->rstate);
+        TRY(rs);
+        for (int lvl = std::min(L1, N - 1); lvl > L0; lvl--)
+          TRY(adjoint_level(c, lvl, c->d_hist + (size_t)(lvl - L0) * hstep, nb, hstride));
+        return FWI_OK;
+      }));
     }
   }
   fwi::launch_check_finite(c->d_gl, (int64_t)nmat, c->d_flag, c->stream);
@@ -1424,6 +1518,15 @@ fwi_status fwi_tune_shot_batch(fwi_ctx *c, int shot0, int nshots, int max_batch,
 fwi_status fwi_set_checkpointing(fwi_ctx *c, int interval) {
   if (!c) return FWI_E_INVAL;
   c->ckpt = interval;
+  return FWI_OK;
+}
+
+fwi_status fwi_set_graphs(fwi_ctx *c, int enable) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->graphs = enable != 0;
+  if (!c->graphs) drop_graphs(c);
   return FWI_OK;
 }
 

@@ -78,6 +78,7 @@ def test_null_context_is_rejected_without_touching_the_gpu():
         "fwi_get_mass_tilde": (nul, nul),
         "fwi_rhs": (nul, 0, nul, nul, 0),
         "fwi_get_state": (nul, nul, 0),
+        "fwi_set_graphs": (nul, 1),
         "fwi_set_timing": (nul, 1),
         "fwi_get_timing": (nul, 0, nul, nul),
         "fwi_reset_timing": (nul,),
