@@ -287,6 +287,22 @@ fwi_status fwi_rhs(fwi_ctx *ctx, int adjoint, const float *state, float *rate, i
  * Errors: FWI_E_INVAL (null), FWI_E_STATE (no state buffers), FWI_E_CUDA. */
 fwi_status fwi_get_state(fwi_ctx *ctx, float *state, int on_device);
 
+/* Persistent forward sweeps: with enable = 1, every later forward sweep (fwi_forward, and
+ * the forward part of fwi_misfit, fwi_adjoint_gradient and fwi_step) of a group of shots
+ * runs as one cooperative kernel launch (one per checkpoint segment) instead of about
+ * 20 launches per RK4 step. All nodes take the general per-node formulas of (3a)/(3b);
+ * the four stages of a step are separated by grid-wide barriers, and source loads,
+ * receiver samples and the displacement history are written by the threads that own
+ * the nodes. Meant for small meshes, where a step is dominated by launch latency; the
+ * results agree with the class-specialised kernels to rounding. Every barrier waits at
+ * most wait_ms milliseconds (0 < wait_ms <= 60000): a barrier that gives up makes the
+ * kernel return, and the call that ran the sweep returns FWI_E_TIMEOUT (the context stays
+ * usable). test_extra_arrivals > 0 makes every barrier wait for that many blocks more
+ * than the launch has, so that the timeout path can be exercised; use 0 otherwise.
+ * The adjoint sweep always uses the specialised kernels. Not in the paper.
+ * Errors: FWI_E_INVAL, FWI_E_NOMEM, FWI_E_CUDA. */
+fwi_status fwi_set_persistent(fwi_ctx *ctx, int enable, double wait_ms, int test_extra_arrivals);
+
 /* CUDA graphs for the time loops: with enable = 1, each sweep of a later call (a forward
  * sweep, the adjoint sweep over the stored history, one checkpoint segment) is recorded by
  * stream capture the first time it runs with a given shot group and replayed as one

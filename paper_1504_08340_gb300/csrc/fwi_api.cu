@@ -94,6 +94,14 @@ struct fwi_ctx {
   bool graphs = false;
   std::vector<Graph> gcache;
 
+  // persistent forward sweeps (fwi_set_persistent)
+  bool persistent = false;
+  double wait_ms = 1000.0;
+  int bar_extra = 0;
+  int *d_all = nullptr, *d_rec_of = nullptr;  // every node; node -> receiver index
+  unsigned *d_bar = nullptr;
+  int *d_status = nullptr;                    // FWI_E_TIMEOUT when a bounded device wait gave up
+
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
@@ -202,7 +210,7 @@ void drop_graphs(fwi_ctx *c) {
 // same arguments in the same order.
 template <class F>
 fwi_status graphed(fwi_ctx *c, int kind, int a, int b, int g, F body) {
-  if (!c->graphs || c->timing) return body();
+  if (!c->graphs || c->timing || c->persistent) return body();
   const uint64_t gen = g_alloc_gen.load();
   for (const auto &e : c->gcache)
     if (e.gen != gen) {
@@ -287,6 +295,20 @@ fwi_status time_flush(fwi_ctx *c) {
   }
   c->ev_pending.clear();
   c->ev_class.clear();
+  return FWI_OK;
+}
+
+// FWI_E_TIMEOUT if a bounded device wait gave up since the last check (synchronises)
+fwi_status check_status(fwi_ctx *c) {
+  if (!c->d_status) return FWI_OK;
+  int st = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (st != 0) {
+    CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return fail(c, FWI_E_TIMEOUT, "a grid barrier of the persistent sweep gave up waiting");
+  }
   return FWI_OK;
 }
 
@@ -415,6 +437,52 @@ fwi_status forward_sweep_body(fwi_ctx *c, int shot0, int nb, float *hist, int64_
       CUDA_TRY(c, cudaMemsetAsync(hist + b * hstride, 0, sizeof(float) * hstep, c->stream));
   fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces, c->stream, nb,
                      (int64_t)sfloats, tf);
+  if (c->persistent) {
+    if (!c->d_rec_of) {
+      std::vector<int> rec_of((size_t)c->geo.stride, -1);
+      for (int r = 0; r < c->nrec; r++) rec_of[(size_t)c->rec_node[r]] = r;
+      TRY(dalloc(c, &c->d_rec_of, rec_of.size()));
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_rec_of, rec_of.data(), sizeof(int) * rec_of.size(), cudaMemcpyHostToDevice,
+                                  c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    // one cooperative launch per checkpoint segment (the whole sweep without snapshots)
+    fwi::PersistArgs p{};
+    for (int b = 0; b < 4; b++) p.st[b] = c->state[b];
+    p.nshot = nb;
+    p.sstride = (int64_t)sfloats;
+    p.dt = (float)c->cfg.dt;
+    p.nodes = c->d_all;
+    p.nall = (int)c->geo.nnode;
+    p.src_node = c->d_src_node + shot0;
+    p.src_vec = c->d_src_vec + 3 * shot0;
+    p.wave = c->d_wave;
+    p.rec_of = c->d_rec_of;
+    p.traces = c->d_traces;
+    p.tstride = tf;
+    p.nrec = c->nrec;
+    p.hist = hist;
+    p.hstep = (int64_t)hstep;
+    p.hstride = hstride;
+    p.bar = c->d_bar;
+    p.extra = c->bar_extra;
+    p.wait_cycles = (long long)(c->wait_ms * 1e-3 * 2.2e9);
+    p.status = c->d_status;
+    const int seg = snap ? every : c->cfg.nsteps;
+    for (int n0 = 0; n0 < c->cfg.nsteps; n0 += seg) {
+      if (snap)
+        for (int b = 0; b < nb; b++)
+          CUDA_TRY(c, cudaMemcpyAsync(snap + ((size_t)b * nseg + n0 / every) * sfloats, c->state[0] + b * sfloats,
+                                      sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+      p.n0 = n0;
+      p.n1 = std::min(n0 + seg, c->cfg.nsteps);
+      CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream));
+      CUDA_TRY(c, fwi::launch_persistent_forward(c->geo, p, c->stream));
+      c->t_launch[0] += 4 * (p.n1 - p.n0);  // stage updates done by the launch
+      c->t_launch[3]++;
+    }
+    return FWI_OK;
+  }
   for (int n = 0; n < c->cfg.nsteps; n++) {
     if (snap && n % every == 0)
       for (int b = 0; b < nb; b++)
@@ -479,6 +547,7 @@ fwi_status finish_J(fwi_ctx *c, int nshots, double *J) {
   CUDA_TRY(c, cudaMemcpyAsync(hJ.data(), c->d_J, sizeof(double) * nshots, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  TRY(check_status(c));
   if (flag) return fail(c, FWI_E_NONFINITE, "non-finite value in the computed traces");
   double s = 0.0;
   for (int i = 0; i < nshots; i++) s += hJ[i];
@@ -701,6 +770,10 @@ void fwi_destroy(fwi_ctx *c) {
   dfree(c->d_lam_n);
   dfree(c->d_mu_n);
   drop_graphs(c);
+  dfree(c->d_all);
+  dfree(c->d_rec_of);
+  dfree(c->d_bar);
+  dfree(c->d_status);
   dfree(c->d_shell);
   dfree(c->d_face);
   dfree(c->d_wave);
@@ -873,6 +946,7 @@ fwi_status fwi_set_receivers(fwi_ctx *c, int nrec, const int *node_ijk) {
   CUDA_TRY(c, cudaMemcpy(c->d_rec_vec, vec.data(), sizeof(float) * 3 * nrec, cudaMemcpyHostToDevice));
   c->nrec = nrec;
   c->rec_node = nodes;
+  dfree(c->d_rec_of);  // rebuilt by the next persistent sweep
   return FWI_OK;
 }
 
@@ -890,7 +964,7 @@ fwi_status fwi_forward(fwi_ctx *c, int shot0, int nshots, float *traces, int on_
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return FWI_OK;
+  return check_status(c);
 }
 
 namespace {
@@ -1518,6 +1592,32 @@ fwi_status fwi_tune_shot_batch(fwi_ctx *c, int shot0, int nshots, int max_batch,
 fwi_status fwi_set_checkpointing(fwi_ctx *c, int interval) {
   if (!c) return FWI_E_INVAL;
   c->ckpt = interval;
+  return FWI_OK;
+}
+
+fwi_status fwi_set_persistent(fwi_ctx *c, int enable, double wait_ms, int test_extra_arrivals) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (enable && !(wait_ms > 0.0 && wait_ms <= 60000.0)) return fail(c, FWI_E_INVAL, "wait_ms outside (0, 60000]");
+  if (test_extra_arrivals < 0) return fail(c, FWI_E_INVAL, "negative test_extra_arrivals");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (enable) {
+    if (!c->d_all) {
+      std::vector<int> all((size_t)c->geo.nnode);
+      size_t q = 0;
+      for (int k = 0; k < c->geo.n[2]; k++)
+        for (int j = 0; j < c->geo.n[1]; j++)
+          for (int i = 0; i < c->geo.n[0]; i++) all[q++] = (k * c->geo.n[1] + j) * c->geo.px + i;
+      TRY(dalloc(c, &c->d_all, all.size()));
+      CUDA_TRY(c, cudaMemcpy(c->d_all, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+    }
+    TRY(dalloc(c, &c->d_bar, 2));
+    TRY(dalloc(c, &c->d_status, 1));
+    CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    c->wait_ms = wait_ms;
+    c->bar_extra = test_extra_arrivals;
+  }
+  c->persistent = enable != 0;
   return FWI_OK;
 }
 

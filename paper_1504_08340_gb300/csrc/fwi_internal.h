@@ -80,6 +80,37 @@ int launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s)
 // raises the interior kernel's shared-memory limit on the current device
 cudaError_t prepare_interior();
 
+// A whole forward sweep (steps n0 .. n1 - 1) of nshot shots in one cooperative launch
+// (fwi_stage.cu): every node takes the general per-node formulas of the shell kernel, the
+// four stages of a step are separated by grid-wide barriers, and the source loads, the
+// receiver samples and the displacement history are written by the threads that own the
+// nodes. Each barrier's spin gives up after wait_cycles clock cycles and sets *status to
+// FWI_E_TIMEOUT; the kernel then returns. A barrier waits for gridDim.x + extra arrivals
+// (extra > 0 only to exercise that path).
+struct PersistArgs {
+  float *st[4];               // X, Y2, Y3, Y4 of the batch's first shot (shot b at + b sstride)
+  int nshot;
+  int64_t sstride;
+  int n0, n1;                 // steps t_n -> t_{n+1} of the sweep
+  float dt;
+  const int *nodes;           // every node of the grid, (k, j, i) order
+  int nall;
+  const int64_t *src_node;    // shot b's source node and load vector (dir / M) at src_node[b], src_vec[3 b]
+  const float *src_vec;
+  const float *wave;          // wavelet samples every dt / 2
+  const int *rec_of;          // node -> receiver index, or -1
+  float *traces;              // shot b's traces at traces + b tstride, [n][nrec][3]
+  int64_t tstride;
+  int nrec;
+  float *hist;                // displacement history, level n at hist + n hstep (shot b at + b hstride), or null
+  int64_t hstep, hstride;
+  unsigned *bar;              // [2]: arrival count and generation, zero before the launch
+  int extra;
+  long long wait_cycles;
+  int *status;
+};
+cudaError_t launch_persistent_forward(const Geo &g, const PersistArgs &p, cudaStream_t s);
+
 // Point loads on level-2 displacement rows of buffer `buf`:
 // buf[9*2 + c][node[p]] += cdt * amp_p * vec[p][c], where
 //   mode 0 (sources): amp_p = wave[widx0] (or 0.5*(wave[widx0]+wave[widx1]))

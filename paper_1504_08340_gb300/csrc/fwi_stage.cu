@@ -28,6 +28,8 @@
 // Every output is written once by one thread: no atomics, bitwise reproducible.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fwi_internal.h"
 
 namespace fwi {
@@ -433,7 +435,136 @@ __global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(
   }
 }
 
+// ---- persistent forward sweep (see PersistArgs)
+
+// grid-wide barrier on a global arrival count and generation; the spin gives up after
+// wait_cycles and records FWI_E_TIMEOUT. False when this or an earlier barrier gave up.
+__device__ bool grid_barrier(const PersistArgs &p, unsigned expected) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int ok = 1;
+    volatile unsigned *gen = p.bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(p.bar, 1u) + 1u == expected) {
+      atomicExch(p.bar, 0u);
+      __threadfence();
+      atomicAdd(p.bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if (clock64() - t0 > p.wait_cycles) {
+          atomicExch(p.status, 6);  // FWI_E_TIMEOUT
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int *)p.status != 0) ok = 0;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// displacement component c of a node for the persistent sweep: shell_disp, plus the
+// source load of the shot (forward point load, as point_kernel adds it) and the receiver
+// sample after the last stage
+__device__ __forceinline__ void persist_disp(const Geo &g, const StageArgs &a, const NodeCtx &n,
+                                             const ShellShared &sh, int lane, int c, const PersistArgs &p, int b,
+                                             int step, int stage) {
+  const int64_t S = g.stride;
+  const float *__restrict__ Y = a.Y;
+  const int64_t i0 = (int64_t)c * S + n.node, i1 = (int64_t)(9 + c) * S + n.node, i2 = (int64_t)(18 + c) * S + n.node;
+  if (n.dir) return;
+  const float fsum = sh.f[0][c][lane] + sh.f[1][c][lane] + sh.f[2][c][lane];
+  const float inv_m = n.inv_a / (g.rho * (float)n.nel);
+  const float u0 = __ldg(Y + i0), u1 = __ldg(Y + i1), u2 = __ldg(Y + i2);
+  const float acc = -fsum * inv_m - (n.cb * u2 + n.cc * u1 + n.cd * u0) * n.inv_a;
+  if (n.pml) __stcs(a.out + i0, stage_value(a, i0, u0, u1));
+  const float v1 = stage_value(a, i1, u1, u2);
+  __stcs(a.out + i1, v1);
+  float v2 = stage_value(a, i2, u2, acc);
+  if (n.node == p.src_node[b]) {
+    // stage times t_n, t_n + dt/2, t_n + dt/2, t_n + dt: samples 2n, 2n+1, 2n+1, 2n+2
+    const float amp = p.wave[stage == 0 ? 2 * step : (stage == 3 ? 2 * step + 2 : 2 * step + 1)];
+    v2 += a.cdt * amp * p.src_vec[3 * b + c];
+  }
+  __stcs(a.out + i2, v2);
+  if (a.hist) write_hist(g, a, n.c3[0], n.c3[1], n.c3[2], c, v1);
+  if (stage == 3) {
+    const int r = p.rec_of[n.node];
+    if (r >= 0) p.traces[(int64_t)b * p.tstride + ((int64_t)(step + 1) * p.nrec + r) * 3 + c] = v1;
+  }
+}
+
+__global__ void __launch_bounds__(3 * kShellNodes) persistent_forward_kernel(Geo g, PersistArgs p) {
+  __shared__ ShellShared sh;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int nch = (p.nall + kShellNodes - 1) / kShellNodes;  // node chunks per shot
+  const unsigned expected = gridDim.x + (unsigned)p.extra;
+  const float cdts[4] = {0.5f * p.dt, 0.5f * p.dt, p.dt, p.dt / 6.0f};
+  for (int step = p.n0; step < p.n1; step++) {
+    for (int s = 0; s < 4; s++) {
+      StageArgs a0{};
+      a0.Y = p.st[s];
+      a0.X = p.st[0];
+      a0.Y2 = p.st[1];
+      a0.Y3 = p.st[2];
+      a0.out = p.st[(s + 1) % 4];
+      a0.cdt = cdts[s];
+      a0.stage = s + 1;
+      a0.hist = (s == 3 && p.hist) ? p.hist + (int64_t)(step + 1) * p.hstep : nullptr;
+      a0.nshot = p.nshot;
+      a0.sstride = p.sstride;
+      a0.hstride = p.hstride;
+      for (int ch = blockIdx.x; ch < nch * p.nshot; ch += gridDim.x) {
+        const int b = ch / nch;
+        const StageArgs a = shot_args(a0, b);
+        const int i = (ch % nch) * kShellNodes + lane;
+        const bool live = i < p.nall;
+        NodeCtx n;
+        if (live) {
+          const int node = p.nodes[i];
+          const int I = node % g.px, r = node / g.px;
+          n = node_ctx(g, I, r % g.n[1], r / g.n[1]);
+          if (w == 0) shell_axis<false, 0>(g, a, n, sh, lane);
+          else if (w == 1) shell_axis<false, 1>(g, a, n, sh, lane);
+          else shell_axis<false, 2>(g, a, n, sh, lane);
+        }
+        __syncthreads();
+        if (live) {
+          persist_disp(g, a, n, sh, lane, w, p, b, step, s);
+          shell_stress<false>(g, a, n, sh, lane, w);
+          shell_stress<false>(g, a, n, sh, lane, w + 3);
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(p, expected)) return;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_persistent_forward(const Geo &g, const PersistArgs &p, cudaStream_t s) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_forward_kernel, 3 * kShellNodes, 0);
+  if (e != cudaSuccess) return e;
+  const int chunks = (p.nall + kShellNodes - 1) / kShellNodes * p.nshot;
+  const int grid = std::max(1, std::min(per_sm * nsm, chunks));
+  Geo gg = g;
+  PersistArgs pp = p;
+  void *args[2] = {&gg, &pp};
+  return cudaLaunchCooperativeKernel((const void *)persistent_forward_kernel, dim3(grid), dim3(kShellNodes, 3), args,
+                                     0, s);
+}
 
 int launch_shell(const Geo &g, const StageArgs &a, bool adjoint, cudaStream_t s) {
   int n = 0;

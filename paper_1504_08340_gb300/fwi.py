@@ -50,7 +50,7 @@ class StepInfo(C.Structure):
 # every symbol the header declares; the CPU test checks the library exports them all
 EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_get_dims",
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
-           "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_get_state", "fwi_set_graphs", "fwi_set_timing",
+           "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_get_state", "fwi_set_graphs", "fwi_set_persistent", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
            "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization",
            "fwi_set_shot_batch", "fwi_tune_shot_batch",
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_rhs.argtypes = [P, I, P, P, I]
     lib.fwi_get_state.argtypes = [P, P, I]
     lib.fwi_set_graphs.argtypes = [P, I]
+    lib.fwi_set_persistent.argtypes = [P, I, C.c_double, I]
     lib.fwi_set_timing.argtypes = [P, I]
     lib.fwi_get_timing.argtypes = [P, I, D, I64]
     lib.fwi_reset_timing.argtypes = [P]
@@ -333,6 +334,10 @@ class Context:
         """0: store u at every step; k > 0: snapshot every k steps and recompute;
         k < 0: every ceil(sqrt(nsteps)) steps (fwi_set_checkpointing)."""
         self._check(self.lib.fwi_set_checkpointing(self.ptr, int(interval)))
+
+    def set_persistent(self, enable=True, wait_ms=1000.0, test_extra_arrivals=0):
+        """Forward sweeps as one cooperative launch with bounded grid barriers (fwi_set_persistent)."""
+        self._check(self.lib.fwi_set_persistent(self.ptr, int(enable), float(wait_ms), int(test_extra_arrivals)))
 
     def set_graphs(self, enable=True):
         """Record each sweep once as a CUDA graph and replay it (fwi_set_graphs)."""
