@@ -562,6 +562,9 @@ def run_batched(args, w):
     B = ctx.tune_shot_batch(0, w.nshots, max_batch=min(args.max_batch, w.nshots), steps=min(5, w.nsteps - 1))
     t_tune = time.perf_counter() - t_tune
     ctx.set_shot_batch(B)
+    t_tiles = time.perf_counter()
+    tiles = ctx.tune_tiles(0, w.nshots, steps=min(3, w.nsteps - 1))
+    t_tune += time.perf_counter() - t_tiles
     ctx.set_graphs(not args.no_graphs)
     gl = torch.empty(ctx.mat_shape(), dtype=torch.float64, device=dev)
     gm = torch.empty_like(gl)
@@ -649,7 +652,8 @@ def run_batched(args, w):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "mesh": f"{w.nx}x{w.ny}x{w.nz}+{w.npml} PML, h={w.h} m",
                        "nodes": ctx.nnode, "elements": ctx.nelem, "shots": w.nshots, "shot_batch": B,
-                       "shot_batch_tuning_s": t_tune, "nsteps_per_step": w.nsteps,
+                       "tiles": {"interior_planes_per_block": tiles[0], "pml_pairs_per_segment": tiles[1]},
+                       "autotuning_s": t_tune, "nsteps_per_step": w.nsteps,
                        "nsteps_of_configuration": full_steps, "dt": w.dt, "receivers": nrec,
                        "graphs": not args.no_graphs, "forward_history": "stored every step of the window",
                        "observed": "seeded synthetic traces", "parallelism": f"shot groups x{world}",

@@ -257,6 +257,15 @@ fwi_status fwi_set_shot_batch(fwi_ctx *ctx, int batch);
 fwi_status fwi_tune_shot_batch(fwi_ctx *ctx, int shot0, int nshots, int max_batch, int steps, double mem_fraction,
                                int *chosen);
 
+/* Picks the launch shapes of the stage kernels by measurement: for each candidate (planes
+ * per block of the interior kernel: 4, 8, 16, 32; node pairs per x segment of a PML warp
+ * task: 16, 32) it times `steps` forward RK4 steps (1 <= steps < nsteps) of the first
+ * shot batch of shots [shot0, shot0 + nshots), keeps the fastest for later calls and
+ * returns it in chosen[0] (planes) and chosen[1] (pairs). The shapes change no node's
+ * arithmetic: every result is bitwise the same with any of them. Not in the paper.
+ * Errors: FWI_E_INVAL, FWI_E_STATE, FWI_E_CUDA. */
+fwi_status fwi_tune_tiles(fwi_ctx *ctx, int shot0, int nshots, int steps, int chosen[2]);
+
 /* Current material ([k][j][i] as in fwi_set_material; host or device). */
 fwi_status fwi_get_material(fwi_ctx *ctx, float *lambda, float *mu, int on_device);
 

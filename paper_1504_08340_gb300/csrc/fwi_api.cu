@@ -621,6 +621,8 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   g.stride = (px * nJ * nK + 63) / 64 * 64;
   g.inv_h = (float)(1.0 / cfg->h);
   g.rho = (float)cfg->rho;
+  g.int_kc = 8;
+  g.pml_seg = 32;
   g.inv_rho_h = (float)(1.0 / (cfg->rho * cfg->h));
   g.wdetj = (float)(0.125 * cfg->h * cfg->h * cfg->h);
   c->nelem = (int64_t)(nI / 2) * (nJ / 2) * (nK / 2);
@@ -1586,6 +1588,51 @@ fwi_status fwi_tune_shot_batch(fwi_ctx *c, int shot0, int nshots, int max_batch,
   TRY(st);
   TRY(resize_batch(c, best));
   *chosen = best;
+  return FWI_OK;
+}
+
+fwi_status fwi_tune_tiles(fwi_ctx *c, int shot0, int nshots, int steps, int chosen[2]) {
+  if (!c) return FWI_E_INVAL;
+  TRY(require_ready(c, shot0, nshots));
+  if (!chosen || steps < 1 || steps >= c->cfg.nsteps) return fail(c, FWI_E_INVAL, "invalid tuning arguments");
+  const int nb = std::min(nshots, c->batch);
+  static const int kcs[4] = {4, 8, 16, 32}, segs[2] = {16, 32};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, FWI_E_CUDA, "event creation failed");
+  }
+  drop_graphs(c);  // recorded sweeps hold the launch shapes they were recorded with
+  const fwi::Geo saved = c->geo;
+  int best[2] = {saved.int_kc, saved.pml_seg};
+  float best_ms = -1.f;
+  fwi_status st = FWI_OK;
+  for (int i = 0; i < 4 && st == FWI_OK; i++)
+    for (int j = 0; j < 2 && st == FWI_OK; j++) {
+      c->geo.int_kc = kcs[i];
+      c->geo.pml_seg = segs[j];
+      // one untimed step, then `steps` timed forward RK4 steps of the first batch of shots
+      st = rk4_step(c, false, 0, shot0, nb, nullptr, 0);
+      if (st == FWI_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, FWI_E_CUDA, "event record failed");
+      for (int n = 1; n <= steps && st == FWI_OK; n++) st = rk4_step(c, false, n, shot0, nb, nullptr, 0);
+      float ms = 0.f;
+      if (st == FWI_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = fail(c, FWI_E_CUDA, "tuning timing failed");
+      if (st == FWI_OK && (best_ms < 0.f || ms < best_ms)) {
+        best_ms = ms;
+        best[0] = kcs[i];
+        best[1] = segs[j];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->geo = saved;
+  TRY(st);
+  c->geo.int_kc = best[0];
+  c->geo.pml_seg = best[1];
+  chosen[0] = best[0];
+  chosen[1] = best[1];
   return FWI_OK;
 }
 

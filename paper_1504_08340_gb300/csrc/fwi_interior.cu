@@ -32,9 +32,6 @@ constexpr int kTP = 32;             // node pairs per tile row (64 nodes)
 #ifndef FWI_INT_TY
 #define FWI_INT_TY 8
 #endif
-#ifndef FWI_INT_KC
-#define FWI_INT_KC 8
-#endif
 constexpr int kTY = FWI_INT_TY;     // rows per tile
 // smem row: the tile's 64 nodes with a halo of 2 on each side, from a 16-byte aligned
 // start (at most 2 nodes before the halo), copied in 16-byte chunks
@@ -46,7 +43,6 @@ constexpr int kNF = 3;              // u_x, u_y, u_z
 constexpr int kPS = kNF * kFS;      // floats per plane
 constexpr int kRing = 6;            // planes K-2 .. K+2 in use, K+3 in flight
 constexpr int kSmem = kRing * kPS * (int)sizeof(float);
-constexpr int kKC = FWI_INT_KC;     // planes per block
 
 enum { kC = 0, kL = 1, kR = 2 };
 // side set of a node along an axis: odd coordinate {C}, even {L, R}, top face {R}
@@ -258,15 +254,16 @@ __device__ __forceinline__ void load_plane(const Geo &g, const StageArgs &a, flo
 #endif
 __global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g, StageArgs a0) {
   float *smem = s_ring;
-  const int nzc = (g.box_hi[2] - g.box_lo[2] + kKC) / kKC;  // z chunks per shot
+  const int kc = g.int_kc;                                   // planes per block
+  const int nzc = (g.box_hi[2] - g.box_lo[2] + kc) / kc;     // z chunks per shot
   const StageArgs a = shot_args(a0, blockIdx.z / nzc);
   const int bz = blockIdx.z % nzc;
   const int x0 = g.box_lo[0] - 1 + 2 * kTP * blockIdx.x;  // even: pairs (even, odd)
   const int xs = (x0 - 2) & ~3;                            // first x of the smem rows
   const int sh = x0 - 2 - xs;                              // 0 or 2
   const int y0 = g.box_lo[1] + kTY * blockIdx.y;
-  const int k0 = g.box_lo[2] + kKC * bz;
-  const int k1 = min(k0 + kKC - 1, g.box_hi[2]);
+  const int k0 = g.box_lo[2] + kc * bz;
+  const int k1 = min(k0 + kc - 1, g.box_hi[2]);
   const int IE = x0 + 2 * threadIdx.x, IO = IE + 1, J = y0 + threadIdx.y;
   const bool rowok = J <= g.box_hi[1];
   const bool even_ok = rowok && IE >= g.box_lo[0] && IE <= g.box_hi[0];
@@ -322,7 +319,7 @@ int launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s) {
   if (g.box_hi[0] < g.box_lo[0] || g.box_hi[1] < g.box_lo[1] || g.box_hi[2] < g.box_lo[2]) return 0;
   const int nx = g.box_hi[0] - (g.box_lo[0] - 1) + 1;
   const dim3 grd((nx + 2 * kTP - 1) / (2 * kTP), (g.box_hi[1] - g.box_lo[1] + kTY) / kTY,
-                 (g.box_hi[2] - g.box_lo[2] + kKC) / kKC * a.nshot);
+                 (g.box_hi[2] - g.box_lo[2] + g.int_kc) / g.int_kc * a.nshot);
   interior_kernel<<<grd, dim3(kTP, kTY), kSmem, s>>>(g, a);
   return 1;
 }

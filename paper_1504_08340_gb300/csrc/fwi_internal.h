@@ -33,6 +33,9 @@ struct Geo {
   int nshell;
   const int *face;        // node numbers of the PML nodes on the grid's outer faces
   int nface;
+  // launch shapes (fwi_tune_tiles; they change no node's arithmetic)
+  int int_kc;             // planes per block of interior_kernel
+  int pml_seg;            // node pairs per x segment of a pml_kernel warp task (<= 32)
 };
 
 // One RK4 stage over every node (see fwi_kernels.cu).

@@ -619,9 +619,9 @@ static Region pml_region(const Geo &g) {
   r.tasks_before[0] = 0;
   for (int b = 0; b < r.nbox; b++) {
     r.P[b] = (r.hi[b][0] - (r.lo[b][0] & ~1)) / 2 + 1;
-    r.nseg[b] = (r.P[b] + 31) / 32;
+    r.nseg[b] = (r.P[b] + g.pml_seg - 1) / g.pml_seg;
     r.per[b] = (r.P[b] + r.nseg[b] - 1) / r.nseg[b];
-    r.R[b] = r.per[b] >= 16 ? 1 : 32 / r.per[b];
+    r.R[b] = r.per[b] > 16 ? 1 : 32 / r.per[b];  // rows per warp task: fill the 32 lanes
     int per_plane = 0;
     for (int c = 0; c < 2; c++) {
       const int jf = r.lo[b][1] + ((r.lo[b][1] & 1) != c ? 1 : 0);  // first J of parity c

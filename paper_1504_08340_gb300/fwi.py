@@ -53,7 +53,7 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_get_state", "fwi_set_graphs", "fwi_set_persistent", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
            "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization",
-           "fwi_set_shot_batch", "fwi_tune_shot_batch",
+           "fwi_set_shot_batch", "fwi_tune_shot_batch", "fwi_tune_tiles",
            # include/fwi_precond.h: the learned preconditioner's kernels
            "fwi_nn_conv3d_forward", "fwi_nn_conv3d_backward_data", "fwi_nn_conv3d_backward_weight_work",
            "fwi_nn_conv3d_backward_weight", "fwi_nn_relu_backward", "fwi_nn_mse", "fwi_nn_adam", "fwi_nn_to_bf16",
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_set_checkpointing.argtypes = [P, I]
     lib.fwi_set_shot_batch.argtypes = [P, I]
     lib.fwi_tune_shot_batch.argtypes = [P, I, I, I, I, C.c_double, C.POINTER(I)]
+    lib.fwi_tune_tiles.argtypes = [P, I, I, I, C.POINTER(I)]
     lib.fwi_regularization.argtypes = [P, I, C.c_double, D, P, P, I]
     L, Fl = C.c_int64, C.c_float
     lib.fwi_nn_conv3d_forward.argtypes = [P, P, P, I, I, I, I, I, I, P, P]
@@ -329,6 +330,15 @@ class Context:
         self._check(self.lib.fwi_tune_shot_batch(self.ptr, int(shot0), int(nshots), int(max_batch), int(steps),
                                                  float(mem_fraction), C.byref(b)))
         return b.value
+
+    def tune_tiles(self, shot0=0, nshots=None, steps=5):
+        """Pick the stage kernels' launch shapes by timing forward steps (fwi_tune_tiles);
+        returns (interior planes per block, PML pairs per segment)."""
+        if nshots is None:
+            nshots = self.nshots - shot0
+        out = (C.c_int * 2)()
+        self._check(self.lib.fwi_tune_tiles(self.ptr, int(shot0), int(nshots), int(steps), out))
+        return out[0], out[1]
 
     def set_checkpointing(self, interval):
         """0: store u at every step; k > 0: snapshot every k steps and recompute;

@@ -90,6 +90,7 @@ def test_null_context_is_rejected_without_touching_the_gpu():
         "fwi_regularization": (nul, 0, 0.0, nul, nul, nul, 0),
         "fwi_set_shot_batch": (nul, 2),
         "fwi_tune_shot_batch": (nul, 0, 1, 4, 3, 0.8, nul),
+        "fwi_tune_tiles": (nul, 0, 1, 3, nul),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == inval, name

@@ -211,3 +211,26 @@ def test_sharded_gradient_matches_all_shots():
     assert parts[0][0] + parts[1][0] == pytest.approx(J, rel=1e-12)
     assert rel_l2((parts[0][1] + parts[1][1]).cpu().numpy(), gl.cpu().numpy()) < 1e-12
     assert rel_l2((parts[0][2] + parts[1][2]).cpu().numpy(), gm.cpu().numpy()) < 1e-12
+
+
+def test_tile_tuner_keeps_results_bitwise():
+    """fwi_tune_tiles picks the interior kernel's planes per block and the PML warp task's
+    segment width by timing; the choice changes no node's arithmetic, so traces and
+    gradients are bitwise those of the default shapes."""
+    from paper_1504_08340_gb300 import Context
+
+    for w in (fi.tiny(nx=3, ny=3, nz=2, npml=2, nsteps=40, f0=30.0, nrec_side=3), fi.box_8x8x4()):
+        w.nsteps = 40
+        l0, m0 = (np.ascontiguousarray(a, dtype=np.float32) for a in fi.medium(w, "trial"))
+        with Context(w.nx, w.ny, w.nz, w.npml, w.h, w.dt, w.nsteps, rho=w.rho) as ctx:
+            ctx.set_material(l0, m0)
+            ctx.set_sources(w.sources(), w.source_dirs(), "ricker", w.ricker())
+            ctx.set_receivers(w.receivers())
+            obs = np.ascontiguousarray(fi.synthetic_traces(w.nsteps, ctx.nrec, 9)[None], dtype=np.float32)
+            tr0 = ctx.forward()
+            J0, gl0, gm0 = ctx.adjoint_gradient(obs)
+            kc, seg = ctx.tune_tiles(steps=5)
+            assert kc in (4, 8, 16, 32) and seg in (16, 32)
+            assert np.array_equal(ctx.forward(), tr0)
+            J1, gl1, gm1 = ctx.adjoint_gradient(obs)
+            assert J1 == J0 and np.array_equal(gl1, gl0) and np.array_equal(gm1, gm0)
