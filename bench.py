@@ -126,8 +126,10 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def measured_traffic(workload_name):
-    """DRAM bytes (read + write) per stage launch from the committed ncu summary, or None."""
+def measured_traffic(workload_name, batch=1, nmat=0):
+    """DRAM bytes (read + write) of one stage launch set from the committed ncu summary, or
+    None. A summary taken on one shot is scaled to a launch set of `batch` shots: the state
+    traffic grows with the shots, lambda and mu (8 bytes a material node) are read once."""
     path = os.path.join(ROOT, "profiles", f"stage_traffic_{workload_name}.json")
     try:
         with open(path) as f:
@@ -136,7 +138,12 @@ def measured_traffic(workload_name):
         return None
     if rec.get("csrc_sha256") != kernel_sources_sha256():
         return None
-    return rec.get("dram_bytes_per_stage")
+    one = rec.get("dram_bytes_per_stage")
+    shots = rec.get("shots_per_launch", 1)
+    if one is None or batch == shots:
+        return one
+    mat = 8.0 * nmat
+    return (one - mat) / shots * batch + mat
 
 
 WORKLOADS = {"layered_96x96x48": fi.layered_96x96x48, "grf_64x64x32": fi.grf_64x64x32}
@@ -390,17 +397,22 @@ def run_batch_sweep(args):
     return 0
 
 
-def profile_gradient(w, nsteps, repeats):
-    """Short gradient evaluations on the benchmark mesh (1 GB of state, nsteps + 1 history
-    levels of 13 MB) for ncu captures of the adjoint and gradient kernels."""
+def profile_gradient(w, nsteps, repeats, batch=1):
+    """Short gradient evaluations on the benchmark mesh (nsteps + 1 history levels) for ncu
+    captures of the adjoint and gradient kernels; with the batched workload, `batch` shots
+    per launch."""
     import torch
 
     w.nsteps = nsteps
     dev = torch.device("cuda", 0)
     ctx, obs, _ = setup(w, torch, dev)
-    obs.copy_(torch.tensor(fi.synthetic_traces(nsteps, w.nrec_side ** 2, 7)[None], dtype=torch.float32))
+    nb = min(batch, w.nshots)
+    if nb > 1:
+        ctx.set_shot_batch(nb)
+    obs = torch.tensor(np.stack([fi.synthetic_traces(nsteps, w.nrec_side ** 2, 7 + s) for s in range(nb)]),
+                       dtype=torch.float32, device=dev).contiguous()
     for _ in range(repeats):
-        J, _, _ = ctx.adjoint_gradient(obs)
+        J, _, _ = ctx.adjoint_gradient(obs, 0, nb)
     torch.cuda.synchronize()
     print(json.dumps({"profile_gradient": w.name, "nsteps": nsteps, "repeats": repeats, "misfit": J}))
     ctx.close()
@@ -663,7 +675,8 @@ def run_batched(args, w):
                 "basis": "the measured element-stage rate, with sqrt(N) checkpointing (one extra forward sweep)"},
             "misfit": J,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": (achieved / hbm) if achieved else None, "traffic": measured_traffic(w.name),
+                         "frac": (achieved / hbm) if achieved else None,
+                         "traffic": measured_traffic(w.name, B, ctx.nmat),
                          "kernel": "RK4 stage launch set advancing B shots (interior_kernel, shell_kernel, "
                                    "pml_face_kernel, pml_kernel)", "peak_kind": peak_kind,
                          "bytes_per_launch": per_launch, "bytes_model": "13 state accesses per variable per step",
@@ -726,7 +739,7 @@ def main():
     if args.profile_forward:
         return profile_forward(w, args.profile_forward, max(args.steps, 1), args.max_batch)
     if args.profile_gradient:
-        return profile_gradient(w, args.profile_gradient, max(args.steps, 1))
+        return profile_gradient(w, args.profile_gradient, max(args.steps, 1), args.max_batch)
     if args.impl == "reference":
         return run_reference(args, w)
     if w.nshots > 1:
