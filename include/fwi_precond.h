@@ -76,6 +76,22 @@ fwi_status fwi_nn_mse(const uint16_t *y, const float *t, int64_t n, float *dy, d
 fwi_status fwi_nn_adam(float *master, uint16_t *w, const float *g, float *m, float *v, int64_t n, float lr,
                        float beta1, float beta2, float eps, int t, void *stream);
 
+/* 2x average pooling and nearest-neighbour upsampling between a fine grid D x H x W
+ * and the coarse grid ceil(D/2) x ceil(H/2) x ceil(W/2), for the U-Net's contracting and
+ * expanding paths; coarse cell q covers the fine voxels 2q and 2q + 1 along each axis,
+ * clipped to the fine grid (D, H, W are always the fine sizes).
+ * pool2_forward:     y[c][q] = mean of x[c][p] over the cell (FP32 sum, BF16 result);
+ * pool2_backward:    dx[c][p] = dy[c][q(p)] / (voxels of the cell q(p));
+ * upsample2_forward: y[c][p] = x[c][q(p)];
+ * upsample2_backward: dx[c][q] = sum of dy[c][p] over the cell, in a fixed order.
+ * x, y: BF16 [C][grid]; dy, dx: FP32 [C][grid]. With accumulate != 0 the backward calls
+ * add into dx (the gradient of an activation that also feeds a skip connection). */
+fwi_status fwi_nn_pool2_forward(const uint16_t *x, int C, int D, int H, int W, uint16_t *y, void *stream);
+fwi_status fwi_nn_pool2_backward(const float *dy, int C, int D, int H, int W, int accumulate, float *dx, void *stream);
+fwi_status fwi_nn_upsample2_forward(const uint16_t *x, int C, int D, int H, int W, uint16_t *y, void *stream);
+fwi_status fwi_nn_upsample2_backward(const float *dy, int C, int D, int H, int W, int accumulate, float *dx,
+                                     void *stream);
+
 /* FP32 -> BF16 (round to nearest even) and BF16 -> FP32, n values. */
 fwi_status fwi_nn_to_bf16(const float *x, int64_t n, uint16_t *y, void *stream);
 fwi_status fwi_nn_from_bf16(const uint16_t *x, int64_t n, float *y, void *stream);

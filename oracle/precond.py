@@ -13,7 +13,11 @@ Written from the definitions, one slice per tap:
   - the loss is sum (y - t)^2 / (2 n), with gradient (y - t) / n;
   - Adam is Algorithm 1 of Kingma & Ba (2015) with bias-corrected moments;
   - BF16 keeps the upper 16 bits of an IEEE binary32 value, rounded to nearest with
-    ties to even.
+    ties to even;
+  - the U-Net's 2x average pooling and nearest-neighbour upsampling: coarse cell q of
+    a fine grid covers the fine voxels 2q, 2q + 1 along each axis, clipped to the grid;
+    pooling is the mean over the cell, upsampling copies the cell's value to its voxels,
+    and their backward passes are the transposed maps.
 Arrays are [C][D][H][W] with W fastest; weights [C_out][C_in][27] with kx fastest.
 """
 from __future__ import annotations
@@ -98,3 +102,58 @@ def adam(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mhat = m / (1 - beta1 ** t)
     vhat = v / (1 - beta2 ** t)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def _cell_index(n):
+    """coarse cell of each fine index along an axis of n points, and the cell count"""
+    return np.arange(n) // 2, (n + 1) // 2
+
+
+def pool2(x):
+    """y[c][q] = mean of x[c][p] over the fine voxels p of coarse cell q (clipped)."""
+    x = np.asarray(x, dtype=np.float64)
+    C, D, H, W = x.shape
+    (iz, nz), (iy, ny), (ix, nx) = _cell_index(D), _cell_index(H), _cell_index(W)
+    s = np.zeros((C, nz, ny, nx))
+    cnt = np.zeros((nz, ny, nx))
+    for z in range(D):
+        for y in range(H):
+            for xx in range(W):
+                s[:, iz[z], iy[y], ix[xx]] += x[:, z, y, xx]
+                cnt[iz[z], iy[y], ix[xx]] += 1
+    return s / cnt
+
+
+def pool2_backward(dy, fine_shape):
+    """dx[c][p] = dy[c][q(p)] / (voxels of cell q(p))."""
+    dy = np.asarray(dy, dtype=np.float64)
+    D, H, W = fine_shape
+    (iz, nz), (iy, ny), (ix, nx) = _cell_index(D), _cell_index(H), _cell_index(W)
+    cnt = np.zeros((nz, ny, nx))
+    for z in range(D):
+        for y in range(H):
+            for xx in range(W):
+                cnt[iz[z], iy[y], ix[xx]] += 1
+    g = dy / cnt
+    return g[:, iz][:, :, iy][:, :, :, ix]
+
+
+def upsample2(x, fine_shape):
+    """y[c][p] = x[c][q(p)]."""
+    x = np.asarray(x, dtype=np.float64)
+    D, H, W = fine_shape
+    iz, iy, ix = (np.arange(n) // 2 for n in (D, H, W))
+    return x[:, iz][:, :, iy][:, :, :, ix]
+
+
+def upsample2_backward(dy):
+    """dx[c][q] = sum of dy[c][p] over the fine voxels p of cell q."""
+    dy = np.asarray(dy, dtype=np.float64)
+    C, D, H, W = dy.shape
+    (iz, nz), (iy, ny), (ix, nx) = _cell_index(D), _cell_index(H), _cell_index(W)
+    out = np.zeros((C, nz, ny, nx))
+    for z in range(D):
+        for y in range(H):
+            for xx in range(W):
+                out[:, iz[z], iy[y], ix[xx]] += dy[:, z, y, xx]
+    return out

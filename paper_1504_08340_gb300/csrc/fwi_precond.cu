@@ -241,6 +241,80 @@ __global__ void __launch_bounds__(kT) from_bf16_kernel(const uint16_t *__restric
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) y[i] = bf2f(x[i]);
 }
 
+// ---- 2x pooling and upsampling between a fine grid D x H x W and the coarse grid
+// ceil(D/2) x ceil(H/2) x ceil(W/2); coarse cell q covers fine voxels 2q .. 2q + 1 along each
+// axis, clipped to the fine grid. Activations BF16, gradients FP32.
+struct Cells {
+  int D, H, W, Dc, Hc, Wc;
+  __device__ __forceinline__ int count(int q0, int q1, int q2) const {  // fine voxels of a coarse cell
+    return (2 * q0 + 1 < D ? 2 : 1) * (2 * q1 + 1 < H ? 2 : 1) * (2 * q2 + 1 < W ? 2 : 1);
+  }
+};
+
+// y[c][q] = mean of x[c][p] over the fine voxels p of coarse cell q (FP32 sum, rounded to BF16)
+__global__ void __launch_bounds__(kT) pool2_fwd_kernel(const uint16_t *__restrict__ x, int C, Cells g,
+                                                       uint16_t *__restrict__ y) {
+  const int64_t nc = (int64_t)g.Dc * g.Hc * g.Wc, n = nc * C;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const int64_t c = i / nc, q = i % nc;
+    const int q2 = (int)(q % g.Wc), q1 = (int)((q / g.Wc) % g.Hc), q0 = (int)(q / ((int64_t)g.Wc * g.Hc));
+    const uint16_t *xc = x + c * (int64_t)g.D * g.H * g.W;
+    float s = 0.f;
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++)
+        for (int e = 0; e < 2; e++) {
+          const int z = 2 * q0 + a, yy = 2 * q1 + b, xx = 2 * q2 + e;
+          if (z < g.D && yy < g.H && xx < g.W) s += bf2f(xc[((int64_t)z * g.H + yy) * g.W + xx]);
+        }
+    y[i] = f2bf(s / (float)g.count(q0, q1, q2));
+  }
+}
+
+// dx[c][p] (+)= dy[c][cell(p)] / count(cell(p))
+__global__ void __launch_bounds__(kT) pool2_bwd_kernel(const float *__restrict__ dy, int C, Cells g, int acc,
+                                                       float *__restrict__ dx) {
+  const int64_t nf = (int64_t)g.D * g.H * g.W, n = nf * C;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const int64_t c = i / nf, p = i % nf;
+    const int x2 = (int)(p % g.W), x1 = (int)((p / g.W) % g.H), x0 = (int)(p / ((int64_t)g.W * g.H));
+    const int q0 = x0 >> 1, q1 = x1 >> 1, q2 = x2 >> 1;
+    const float v = dy[c * (int64_t)g.Dc * g.Hc * g.Wc + ((int64_t)q0 * g.Hc + q1) * g.Wc + q2] / (float)g.count(q0, q1, q2);
+    dx[i] = acc ? dx[i] + v : v;
+  }
+}
+
+// y[c][p] = x[c][cell(p)] (nearest neighbour)
+__global__ void __launch_bounds__(kT) up2_fwd_kernel(const uint16_t *__restrict__ x, int C, Cells g,
+                                                     uint16_t *__restrict__ y) {
+  const int64_t nf = (int64_t)g.D * g.H * g.W, n = nf * C;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const int64_t c = i / nf, p = i % nf;
+    const int x2 = (int)(p % g.W), x1 = (int)((p / g.W) % g.H), x0 = (int)(p / ((int64_t)g.W * g.H));
+    y[i] = x[c * (int64_t)g.Dc * g.Hc * g.Wc + ((int64_t)(x0 >> 1) * g.Hc + (x1 >> 1)) * g.Wc + (x2 >> 1)];
+  }
+}
+
+// dx[c][q] (+)= sum of dy[c][p] over the fine voxels p of cell q, in a fixed order
+__global__ void __launch_bounds__(kT) up2_bwd_kernel(const float *__restrict__ dy, int C, Cells g, int acc,
+                                                     float *__restrict__ dx) {
+  const int64_t nc = (int64_t)g.Dc * g.Hc * g.Wc, n = nc * C;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const int64_t c = i / nc, q = i % nc;
+    const int q2 = (int)(q % g.Wc), q1 = (int)((q / g.Wc) % g.Hc), q0 = (int)(q / ((int64_t)g.Wc * g.Hc));
+    const float *dc = dy + c * (int64_t)g.D * g.H * g.W;
+    float s = 0.f;
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++)
+        for (int e = 0; e < 2; e++) {
+          const int z = 2 * q0 + a, yy = 2 * q1 + b, xx = 2 * q2 + e;
+          if (z < g.D && yy < g.H && xx < g.W) s += dc[((int64_t)z * g.H + yy) * g.W + xx];
+        }
+    dx[i] = acc ? dx[i] + s : s;
+  }
+}
+
+Cells cells(int D, int H, int W) { return Cells{D, H, W, (D + 1) / 2, (H + 1) / 2, (W + 1) / 2}; }
+
 bool sizes_ok(int cin, int cout, int D, int H, int W) {
   if (cin < 1 || cout < 1 || D < 1 || H < 1 || W < 1) return false;
   if (cin > 65535 || cout > 65535) return false;  // grid y / z limits
@@ -321,6 +395,35 @@ fwi_status fwi_nn_adam(float *master, uint16_t *w, const float *g, float *m, flo
   const double p1 = std::pow((double)beta1, t), p2 = std::pow((double)beta2, t);
   adam_kernel<<<grid_for(n), kT, 0, (cudaStream_t)stream>>>(master, w, g, m, v, n, lr, beta1, beta2, eps,
                                                             (float)(1.0 / (1.0 - p1)), (float)(1.0 / (1.0 - p2)));
+  return launched();
+}
+
+fwi_status fwi_nn_pool2_forward(const uint16_t *x, int C, int D, int H, int W, uint16_t *y, void *stream) {
+  if (!x || !y || !sizes_ok(C, 1, D, H, W)) return FWI_E_INVAL;
+  const Cells g = cells(D, H, W);
+  pool2_fwd_kernel<<<grid_for((int64_t)C * g.Dc * g.Hc * g.Wc), kT, 0, (cudaStream_t)stream>>>(x, C, g, y);
+  return launched();
+}
+
+fwi_status fwi_nn_pool2_backward(const float *dy, int C, int D, int H, int W, int accumulate, float *dx, void *stream) {
+  if (!dy || !dx || !sizes_ok(C, 1, D, H, W)) return FWI_E_INVAL;
+  pool2_bwd_kernel<<<grid_for((int64_t)C * D * H * W), kT, 0, (cudaStream_t)stream>>>(dy, C, cells(D, H, W),
+                                                                                      accumulate != 0, dx);
+  return launched();
+}
+
+fwi_status fwi_nn_upsample2_forward(const uint16_t *x, int C, int D, int H, int W, uint16_t *y, void *stream) {
+  if (!x || !y || !sizes_ok(C, 1, D, H, W)) return FWI_E_INVAL;
+  up2_fwd_kernel<<<grid_for((int64_t)C * D * H * W), kT, 0, (cudaStream_t)stream>>>(x, C, cells(D, H, W), y);
+  return launched();
+}
+
+fwi_status fwi_nn_upsample2_backward(const float *dy, int C, int D, int H, int W, int accumulate, float *dx,
+                                     void *stream) {
+  if (!dy || !dx || !sizes_ok(C, 1, D, H, W)) return FWI_E_INVAL;
+  const Cells g = cells(D, H, W);
+  up2_bwd_kernel<<<grid_for((int64_t)C * g.Dc * g.Hc * g.Wc), kT, 0, (cudaStream_t)stream>>>(dy, C, g,
+                                                                                             accumulate != 0, dx);
   return launched();
 }
 

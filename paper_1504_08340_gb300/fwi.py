@@ -56,7 +56,8 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
            "fwi_set_shot_batch", "fwi_tune_shot_batch", "fwi_tune_tiles",
            # include/fwi_precond.h: the learned preconditioner's kernels
            "fwi_nn_conv3d_forward", "fwi_nn_conv3d_backward_data", "fwi_nn_conv3d_backward_weight_work",
-           "fwi_nn_conv3d_backward_weight", "fwi_nn_relu_backward", "fwi_nn_mse", "fwi_nn_adam", "fwi_nn_to_bf16",
+           "fwi_nn_conv3d_backward_weight", "fwi_nn_relu_backward", "fwi_nn_mse", "fwi_nn_adam", "fwi_nn_pool2_forward",
+           "fwi_nn_pool2_backward", "fwi_nn_upsample2_forward", "fwi_nn_upsample2_backward", "fwi_nn_to_bf16",
            "fwi_nn_from_bf16")
 
 _lib = None
@@ -112,6 +113,10 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_nn_relu_backward.argtypes = [P, P, L, P, P]
     lib.fwi_nn_mse.argtypes = [P, P, L, P, P, P, P]
     lib.fwi_nn_adam.argtypes = [P, P, P, P, P, L, Fl, Fl, Fl, Fl, I, P]
+    lib.fwi_nn_pool2_forward.argtypes = [P, I, I, I, I, P, P]
+    lib.fwi_nn_pool2_backward.argtypes = [P, I, I, I, I, I, P, P]
+    lib.fwi_nn_upsample2_forward.argtypes = [P, I, I, I, I, P, P]
+    lib.fwi_nn_upsample2_backward.argtypes = [P, I, I, I, I, I, P, P]
     lib.fwi_nn_to_bf16.argtypes = [P, L, P, P]
     lib.fwi_nn_from_bf16.argtypes = [P, L, P, P]
     for name in EXPORTS:

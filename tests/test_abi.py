@@ -110,5 +110,9 @@ def test_null_context_is_rejected_without_touching_the_gpu():
     assert lib.fwi_nn_mse(one, one, 10, one, nul, one, nul) == inval
     assert lib.fwi_nn_adam(one, nul, one, one, one, 10, 1e-3, 0.9, 0.999, 1e-8, 0, nul) == inval
     assert lib.fwi_nn_adam(one, nul, one, one, one, 10, 1e-3, 1.0, 0.999, 1e-8, 1, nul) == inval
+    assert lib.fwi_nn_pool2_forward(nul, 1, 2, 2, 2, one, nul) == inval
+    assert lib.fwi_nn_pool2_backward(one, 0, 2, 2, 2, 0, one, nul) == inval
+    assert lib.fwi_nn_upsample2_forward(one, 1, 2, 0, 2, one, nul) == inval
+    assert lib.fwi_nn_upsample2_backward(one, 1, 2, 2, 2, 1, nul, nul) == inval
     assert lib.fwi_nn_to_bf16(nul, 4, one, nul) == inval
     assert lib.fwi_nn_from_bf16(one, 4, nul, nul) == inval

@@ -94,3 +94,25 @@ def test_bf16_rounding():
     ref = torch.tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(P.bf16_round(x), ref)
     assert np.array_equal(P.bf16_value(P.bf16_bits(x)), ref)
+
+
+@pytest.mark.parametrize("shape", [(4, 6, 8), (5, 7, 9), (1, 3, 2)])
+def test_pool_and_upsample_pins(shape):
+    """Pooling a constant field gives the constant; pooling what upsampling produced gives
+    the coarse field back (every voxel of a cell holds its value); the backward passes are
+    the transposed maps (dot-product test); a brute-force mean on one cell."""
+    rng = _rng(21)
+    C = 3
+    x = rng.standard_normal((C,) + shape)
+    cz, cy, cx = ((n + 1) // 2 for n in shape)
+    assert np.allclose(P.pool2(np.full((C,) + shape, 2.5)), 2.5, rtol=0, atol=1e-15)
+    xc = rng.standard_normal((C, cz, cy, cx))
+    assert np.allclose(P.pool2(P.upsample2(xc, shape)), xc, rtol=0, atol=1e-14)
+    dyc = rng.standard_normal((C, cz, cy, cx))
+    assert np.isclose((P.pool2(x) * dyc).sum(), (x * P.pool2_backward(dyc, shape)).sum(), rtol=1e-12)
+    dyf = rng.standard_normal((C,) + shape)
+    assert np.isclose((P.upsample2(xc, shape) * dyf).sum(), (xc * P.upsample2_backward(dyf)).sum(), rtol=1e-12)
+    # the last cell along every axis of an odd grid holds one voxel along that axis
+    q = (cz - 1, cy - 1, cx - 1)
+    block = x[:, 2 * q[0]:2 * q[0] + 2, 2 * q[1]:2 * q[1] + 2, 2 * q[2]:2 * q[2] + 2]
+    assert np.allclose(P.pool2(x)[:, q[0], q[1], q[2]], block.reshape(C, -1).mean(axis=1), rtol=1e-14)
