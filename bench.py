@@ -697,6 +697,125 @@ def run_batched(args, w):
     return 0
 
 
+def run_precond_study(args):
+    """The learned preconditioner end to end, on the 16x16x8 + 10 PML box (one shot, 600
+    steps): training pairs (gradient, model) -> remaining model error from the plain
+    inversion (the library's L-BFGS, fwi_step) on --study-train seeded random media,
+    the U-Net trained on them, and --study-test held-out media inverted for
+    --study-iters iterations by plain L-BFGS and by the network's updates with a
+    backtracking line search. One JSON line with the per-iteration means of the misfit
+    and of the lambda / mu model errors, and the wall seconds."""
+    import torch
+
+    from paper_1504_08340_gb300 import Context, FWIError
+    from paper_1504_08340_gb300.precond import UNet, learned_update, precond_inputs, precond_targets
+
+    dev = torch.device("cuda", 0)
+    w0 = fi.media_16x16x8(0)
+    lam_bg, mu_bg = (float(a.flat[0]) for a in fi.medium(w0, "trial"))
+    ctx = Context(w0.nx, w0.ny, w0.nz, w0.npml, w0.h, w0.dt, w0.nsteps, rho=w0.rho)
+    ctx.set_sources(w0.sources(), w0.source_dirs(), "ricker", w0.ricker())
+    ctx.set_receivers(w0.receivers())
+    ctx.set_graphs(True)
+    l0, m0 = (torch.tensor(a, dtype=torch.float32, device=dev) for a in fi.medium(w0, "trial"))
+    obs = torch.zeros(ctx.trace_shape(1), dtype=torch.float32, device=dev)
+
+    def truth(seed):
+        lt, mt = (torch.tensor(a, dtype=torch.float32, device=dev) for a in fi.medium(fi.media_16x16x8(seed), "true"))
+        ctx.set_material(lt, mt)
+        ctx.forward(out=obs)
+        return lt, mt
+
+    def errors(lt, mt):
+        lam, mu = (torch.tensor(a, device=dev) for a in ctx.get_material())
+        return (float(torch.linalg.vector_norm(lam - lt) / torch.linalg.vector_norm(l0 - lt)),
+                float(torch.linalg.vector_norm(mu - mt) / torch.linalg.vector_norm(m0 - mt)))
+
+    # ---- training pairs along the plain inversion
+    t0 = time.perf_counter()
+    xs, ts = [], []
+    for k in range(args.study_train):
+        lt, mt = truth(1000 + k)
+        ctx.set_material(l0, m0)
+        ctx.step_reset()
+        for it in range(args.study_pair_iters + 1):
+            _, gl, gm = ctx.adjoint_gradient(obs)
+            lam, mu = (torch.tensor(a, device=dev) for a in ctx.get_material())
+            xs.append(precond_inputs(gl, gm, lam, mu, lam_bg, mu_bg))
+            ts.append(precond_targets(lt, mt, lam, mu, lam_bg, mu_bg))
+            if it < args.study_pair_iters:
+                ctx.step(obs, first_step=0.05)
+    t_pairs = time.perf_counter() - t0
+    # ---- training
+    net = UNet(4, 2, tuple(args.study_widths), ctx.mat_shape(), seed=0, lr=args.study_lr)
+    xb = [net.to_bf16(x) for x in xs]
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    losses = []
+    for step in range(args.study_train_steps):
+        i = int(rng.integers(len(xb)))
+        losses.append(net.train_step(xb[i], ts[i]))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # ---- evaluation on held-out media
+    hist = {"plain": [], "learned": []}
+    for k in range(args.study_test):
+        lt, mt = truth(5000 + k)
+        for method in ("plain", "learned"):
+            ctx.set_material(l0, m0)
+            ctx.step_reset()
+            J = ctx.misfit(obs)
+            rec = [(0.0, J, *errors(lt, mt))]
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for it in range(args.study_iters):
+                if method == "plain":
+                    J = ctx.step(obs, first_step=0.05).J_new
+                else:
+                    J, gl, gm = ctx.adjoint_gradient(obs)
+                    lam, mu = (torch.tensor(a, device=dev) for a in ctx.get_material())
+                    dl, dm = learned_update(net, gl, gm, lam, mu, lam_bg, mu_bg)
+                    gtd = float((gl * dl).sum() + (gm * dm).sum())
+                    if not gtd < 0:  # not a descent direction: steepest descent, 5 % of the model
+                        s_ = 0.05 * float(torch.maximum(lam.abs().max(), mu.abs().max())) / float(
+                            torch.maximum(gl.abs().max(), gm.abs().max()))
+                        dl, dm = -s_ * gl, -s_ * gm
+                        gtd = float((gl * dl).sum() + (gm * dm).sum())
+                    alpha, Jn = 1.0, None
+                    for _ in range(8):  # Armijo backtracking (Algorithm 1), c1 = 1e-4
+                        tl, tm = (lam + alpha * dl).clamp_min(1.0), (mu + alpha * dm).clamp_min(1.0)
+                        try:  # a trial beyond the time-step limit counts as a rejected trial
+                            ctx.set_material(tl.to(torch.float32).contiguous(), tm.to(torch.float32).contiguous())
+                            Jn = ctx.misfit(obs)
+                        except FWIError:
+                            Jn = float("inf")
+                        if Jn <= J + 1e-4 * alpha * gtd:
+                            break
+                        alpha *= 0.5
+                    else:
+                        ctx.set_material(lam.to(torch.float32).contiguous(), mu.to(torch.float32).contiguous())
+                        Jn = J
+                    J = Jn
+                torch.cuda.synchronize()
+                rec.append((time.perf_counter() - t, J, *errors(lt, mt)))
+            hist[method].append(rec)
+    out = {"metric": "learned preconditioner study", "workload": "media_16x16x8 (16x16x8 + 10 PML, 600 steps, 1 shot)",
+           "network": {"widths": list(args.study_widths), "params": net.num_params(), "steps": args.study_train_steps,
+                       "loss_first": float(np.mean(losses[:50])), "loss_last": float(np.mean(losses[-50:]))},
+           "pairs": len(xs), "train_media": args.study_train, "test_media": args.study_test,
+           "seconds": {"pairs": t_pairs, "training": t_train}}
+    for method, recs in hist.items():
+        a = np.array(recs)  # [media][iteration][t, J, err_lambda, err_mu]
+        J0 = a[:, :1, 1]
+        out[method] = {"seconds": a[:, :, 0].mean(0).round(3).tolist(),
+                       "misfit_rel": (a[:, :, 1] / J0).mean(0).round(5).tolist(),
+                       "err_lambda": a[:, :, 2].mean(0).round(5).tolist(),
+                       "err_mu": a[:, :, 3].mean(0).round(5).tolist()}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -729,7 +848,18 @@ def main():
     ap.add_argument("--max-batch", type=int, default=16, help="largest shot batch the autotuner may pick")
     ap.add_argument("--no-graphs", action="store_true", help="direct launches instead of replayed CUDA graphs")
     ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
+    ap.add_argument("--precond-study", action="store_true",
+                    help="instead of the headline benchmark: train and evaluate the learned preconditioner")
+    ap.add_argument("--study-train", type=int, default=200)
+    ap.add_argument("--study-test", type=int, default=20)
+    ap.add_argument("--study-iters", type=int, default=10)
+    ap.add_argument("--study-pair-iters", type=int, default=2)
+    ap.add_argument("--study-train-steps", type=int, default=3000)
+    ap.add_argument("--study-lr", type=float, default=3e-4)
+    ap.add_argument("--study-widths", type=int, nargs=3, default=[28, 56, 112])
     args = ap.parse_args()
+    if args.precond_study:
+        return run_precond_study(args)
     if args.precond_bench:
         return run_precond_bench(args)
     if args.shot_batch_sweep:

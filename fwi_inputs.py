@@ -144,6 +144,10 @@ def medium(w: Workload, which: str = "true"):
         else:
             d = np.zeros(shape)
         return lame_from_velocities(200.0 * (1 + d), 400.0 * (1 + d), w.rho)
+    if w.name.startswith("media"):
+        if which == "true":
+            return random_medium(w, w.seed)
+        return lame_from_velocities(np.full(shape, 200.0), np.full(shape, 400.0), w.rho)
     if w.name.startswith("layered"):
         r = vp_over_vs(0.3)
         Z, Y, X = _grid(w)
@@ -157,6 +161,29 @@ def medium(w: Workload, which: str = "true"):
             vs = np.full(shape, 150.0)
         return lame_from_velocities(vs, r * vs, w.rho)
     raise ValueError(w.name)
+
+
+def random_medium(w: Workload, seed: int):
+    """(lambda, mu) of a seeded random medium of the learned-preconditioner study: a Gaussian
+    random field (correlation length 8 m, max |delta| = 0.2 on Vs 200 and Vp 400 m/s) plus
+    0-3 sharp ellipsoidal inclusions, each scaling the background Vs and Vp by 1 + c with c in
+    [-0.3, 0.3] (a later inclusion overrides an earlier one where they overlap) and semi-axes of
+    1.5-4 m, centred inside the interior."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = w.mat_shape
+    d = gaussian_random_field(shape, 8.0 / (0.5 * w.h), int(rng.integers(1 << 30)), 0.2)
+    vs0 = 200.0 * (1 + d)
+    vp0 = 400.0 * (1 + d)
+    vs, vp = vs0.copy(), vp0.copy()
+    Z, Y, X = _grid(w)
+    for _ in range(int(rng.integers(0, 4))):
+        c = (rng.uniform(0.2, 0.8) * w.nx * w.h, rng.uniform(0.2, 0.8) * w.ny * w.h, rng.uniform(0.2, 0.8) * w.nz * w.h)
+        r = rng.uniform(1.5, 4.0, 3)
+        inside = ((X - c[0]) / r[0]) ** 2 + ((Y - c[1]) / r[1]) ** 2 + ((Z - c[2]) / r[2]) ** 2 <= 1.0
+        f = 1.0 + rng.uniform(-0.3, 0.3)
+        vs = np.where(inside, vs0 * f, vs)  # scales the background: overlaps do not compound
+        vp = np.where(inside, vp0 * f, vp)
+    return lame_from_velocities(vs, vp, w.rho)
 
 
 def vp_max(w: Workload):
@@ -180,6 +207,15 @@ def grf_64x64x32():  # single shot, smooth Gaussian random field, 2000 steps, 32
 
 def grf_16x16x8():  # the single-shot recipe (GRF, 10-element PML, f0, dt, 2000 steps) on a 16x16x8 box
     return build(Workload("grf_16x16x8", 16, 16, 8, 10, 1.0, 2000, 10.0, 8, seed=2))
+
+
+def media_16x16x8(seed=0):
+    """A seeded random medium of the learned-preconditioner study: 16x16x8 + 10 PML, one
+    surface shot (Ricker 20 Hz), 600 steps, 8x8 receivers; the time step covers every medium
+    the generator can draw (Vp at most 400 x 1.2 x 1.3 m/s)."""
+    w = Workload("media_16x16x8", 16, 16, 8, 10, 1.0, 600, 20.0, 8, seed=seed)
+    w.dt = cfl_dt(w.h, 400.0 * 1.2 * 1.3, w.cfl)
+    return w
 
 
 def layered_96x96x48():  # 3 layers + sharp inclusion, 16 shots, 3000 steps, 48x48 receivers

@@ -339,3 +339,40 @@ class UNet:
             self._check(self.lib.fwi_nn_adam(_p(l.b), None, _p(l.g_b), _p(l.m_b), _p(l.v_b), l.b.numel(), self.lr,
                                              b1, b2, self.eps, self.t, s))
         return float(self.loss_dev.item())
+
+
+def precond_inputs(g_lambda, g_mu, lam, mu, lam_bg, mu_bg):
+    """The network input [4][D][H][W] (FP32, on the gradients' device) for one model: the
+    misfit gradients scaled together by their largest magnitude (their ratio, where the
+    lambda-mu cross-talk shows, is kept), and the model as relative perturbations of the
+    background values lam_bg, mu_bg."""
+    import torch
+
+    gl = torch.as_tensor(g_lambda).to(torch.float64)
+    gm = torch.as_tensor(g_mu).to(gl.device, torch.float64)
+    scale = torch.maximum(gl.abs().max(), gm.abs().max()).clamp_min(1e-300)
+    lam = torch.as_tensor(lam).to(gl.device, torch.float64)
+    mu = torch.as_tensor(mu).to(gl.device, torch.float64)
+    x = torch.stack([gl / scale, gm / scale, lam / lam_bg - 1.0, mu / mu_bg - 1.0])
+    return x.to(torch.float32).contiguous()
+
+
+def precond_targets(lam_true, mu_true, lam, mu, lam_bg, mu_bg):
+    """The training target [2][D][H][W]: the remaining model error (true minus current) of
+    lambda and mu, relative to the background values."""
+    import torch
+
+    lt = torch.as_tensor(lam_true).to(torch.float64)
+    d = lt.device
+    t = torch.stack([(lt - torch.as_tensor(lam).to(d, torch.float64)) / lam_bg,
+                     (torch.as_tensor(mu_true).to(d, torch.float64) - torch.as_tensor(mu).to(d, torch.float64)) / mu_bg])
+    return t.to(torch.float32).contiguous()
+
+
+def learned_update(net, g_lambda, g_mu, lam, mu, lam_bg, mu_bg):
+    """The model update (d_lambda, d_mu) in Pa that the network proposes for a model and its
+    misfit gradients (FP64 tensors on the network's device)."""
+    import torch
+
+    y = net(precond_inputs(g_lambda, g_mu, lam, mu, lam_bg, mu_bg).to(net.device)).to(torch.float64)
+    return y[0] * lam_bg, y[1] * mu_bg

@@ -85,3 +85,20 @@ def test_synthetic_traces_are_seeded():
     assert a.shape == (21, 4, 3)
     assert np.array_equal(a, fi.synthetic_traces(20, 4, 7))
     assert not np.array_equal(a, fi.synthetic_traces(20, 4, 8))
+
+
+def test_random_media_of_the_preconditioner_study():
+    """GRF about Vs 200 / Vp 400 within the generator's bounds, seeded (same seed, same
+    medium), and the time step at Courant 0.5 for the fastest medium the generator allows."""
+    vmax = 0.0
+    for seed in range(12):
+        w = fi.media_16x16x8(seed)
+        vs, vp = _velocities(w, "true")
+        assert np.allclose(vp / vs, 2.0)
+        assert vs.min() >= 200 * 0.8 * 0.7 - 1e-9 and vs.max() <= 200 * 1.2 * 1.3 + 1e-9
+        vmax = max(vmax, vp.max())
+        lam2, mu2 = fi.medium(fi.media_16x16x8(seed), "true")
+        assert np.array_equal(lam2, fi.medium(w, "true")[0]) and np.array_equal(mu2, fi.medium(w, "true")[1])
+        assert 0.5 * 0.5 * w.h / w.dt >= vmax
+    vs0, vp0 = _velocities(fi.media_16x16x8(0), "trial")
+    assert np.all(vs0 == 200.0) and np.all(vp0 == 400.0)
