@@ -799,9 +799,11 @@ def run_precond_study(args):
                 torch.cuda.synchronize()
                 rec.append((time.perf_counter() - t, J, *errors(lt, mt)))
             hist[method].append(rec)
+    win = max(1, min(50, len(losses) // 10))  # mean loss over the first and the last tenth (at most 50 steps)
     out = {"metric": "learned preconditioner study", "workload": "media_16x16x8 (16x16x8 + 10 PML, 600 steps, 1 shot)",
            "network": {"widths": list(args.study_widths), "params": net.num_params(), "steps": args.study_train_steps,
-                       "loss_first": float(np.mean(losses[:50])), "loss_last": float(np.mean(losses[-50:]))},
+                       "loss_window": win, "loss_first": float(np.mean(losses[:win])),
+                       "loss_last": float(np.mean(losses[-win:]))},
            "pairs": len(xs), "train_media": args.study_train, "test_media": args.study_test,
            "seconds": {"pairs": t_pairs, "training": t_train}}
     for method, recs in hist.items():
