@@ -818,6 +818,153 @@ def run_precond_study(args):
     return 0
 
 
+def _bytes_in_use(torch, dev):
+    free, total = torch.cuda.mem_get_info(dev)
+    return total - free
+
+
+def run_full_evaluation(args):
+    """One-off measurement: the whole 16-shot gradient evaluation of the layered workload at
+    its full 3000 steps, observed traces computed from the true medium, the adjoint fed by
+    sqrt(T) compact snapshots with recompute, shots in groups of --full-batch, each sweep a
+    replayed CUDA graph. --steps evaluations are timed after --warmup (default 0 here: one
+    evaluation is minutes of GPU work; its one-time graph recording and allocations are
+    under a second of it). One JSON line."""
+    import math
+
+    import torch
+
+    from paper_1504_08340_gb300 import Context
+
+    w = fi.layered_96x96x48()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = _bytes_in_use(torch, dev)
+    ctx = Context(w.nx, w.ny, w.nz, w.npml, w.h, w.dt, w.nsteps, rho=w.rho)
+    ctx.set_sources(w.sources(), w.source_dirs(), "ricker", w.ricker())
+    ctx.set_receivers(w.receivers())
+    ctx.set_shot_batch(args.full_batch)
+    ctx.set_graphs(True)
+    lt, mt = (torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev) for a in fi.medium(w, "true"))
+    l0, m0 = (torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev) for a in fi.medium(w, "trial"))
+    obs = torch.empty(ctx.trace_shape(w.nshots), dtype=torch.float32, device=dev)
+    t = time.perf_counter()
+    ctx.set_material(lt, mt)
+    ctx.forward(0, w.nshots, out=obs)
+    torch.cuda.synchronize()
+    t_obs = time.perf_counter() - t
+    ctx.set_material(l0, m0)
+    ctx.set_checkpointing(-1)
+    gl = torch.empty(ctx.mat_shape(), dtype=torch.float64, device=dev)
+    gm = torch.empty_like(gl)
+    for _ in range(args.warmup):
+        ctx.adjoint_gradient(obs, 0, w.nshots, g_lambda=gl, g_mu=gm)
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        J, _, _ = ctx.adjoint_gradient(obs, 0, w.nshots, g_lambda=gl, g_mu=gm)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    every = math.ceil(math.sqrt(w.nsteps))
+    work = ctx.nelem * 4 * w.nsteps * 2 * w.nshots  # forward and adjoint sweeps; the recompute is not counted
+    print(json.dumps({
+        "metric": "full-length 16-shot gradient evaluations/s", "value": 1e3 / ms, "unit": "evaluations/s",
+        "workload": "layered_96x96x48", "nsteps": w.nsteps, "shots": w.nshots, "shot_batch": args.full_batch,
+        "checkpoint": {"interval": every, "snapshots_per_shot": math.ceil(w.nsteps / every), "kind": "compact"},
+        "observed": "forward traces of the true medium", "warmup": args.warmup, "steps": args.steps,
+        "seconds_per_evaluation": ms / 1e3, "shot_gradient_evals_per_s": w.nshots * 1e3 / ms,
+        "element_stage_updates_per_s": work / (ms / 1e3), "J": J, "observed_forward_s": t_obs,
+        "device_bytes": _bytes_in_use(torch, dev) - base, "clocks": clocks}))
+
+
+def run_large_iteration(args):
+    """One-off measurement: one torch.autograd-driven inversion iteration on the large
+    workload (160x160x80 + 12 PML, 64 shots, 4000 steps, 80x80 receivers) over its first
+    --large-shots shots. Observed traces come from the true medium; J and g_mis come from
+    MisfitFunction (forward, misfit, adjoint with sqrt(T) compact snapshots); the direction
+    is -M~^-1 g_mis scaled to max |d| = 5 % of max |m|; Armijo backtracking (Algorithm 1,
+    c1 = 1e-4, halving) evaluates misfit-only trials. One JSON line with the seconds of
+    each part and the device memory the context holds."""
+    import math
+
+    import torch
+
+    from paper_1504_08340_gb300 import Context, FWIError
+    from paper_1504_08340_gb300.autograd import misfit
+
+    w = fi.large_160x160x80()
+    S = args.large_shots
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = _bytes_in_use(torch, dev)
+    ctx = Context(w.nx, w.ny, w.nz, w.npml, w.h, w.dt, w.nsteps, rho=w.rho)
+    ctx.set_sources(w.sources(), w.source_dirs(), "ricker", w.ricker())
+    ctx.set_receivers(w.receivers())
+    ctx.set_shot_batch(min(S, args.full_batch))
+    ctx.set_graphs(True)
+    lt, mt = (torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev) for a in fi.medium(w, "true"))
+    l0, m0 = (np.ascontiguousarray(a, dtype=np.float32) for a in fi.medium(w, "trial"))
+    obs = torch.empty(ctx.trace_shape(S), dtype=torch.float32, device=dev)
+    t = time.perf_counter()
+    ctx.set_material(lt, mt)
+    ctx.forward(0, S, out=obs)
+    torch.cuda.synchronize()
+    t_obs = time.perf_counter() - t
+    del lt, mt
+    ctx.set_checkpointing(-1)
+    lam = torch.tensor(l0, device=dev, requires_grad=True)
+    mu = torch.tensor(m0, device=dev, requires_grad=True)
+    t = time.perf_counter()
+    J = misfit(ctx, lam, mu, obs, 0, S)
+    J.backward()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t
+    held = _bytes_in_use(torch, dev) - base
+    J0 = float(J)
+    mt_inv = 1.0 / torch.tensor(ctx.mass_tilde(), device=dev)
+    gl, gm = lam.grad.double(), mu.grad.double()
+    ml, mm = lam.detach().double(), mu.detach().double()
+    dl, dm = -mt_inv * gl, -mt_inv * gm
+    scale = 0.05 * float(torch.maximum(ml.abs().max(), mm.abs().max())) / float(torch.maximum(dl.abs().max(), dm.abs().max()))
+    dl, dm = scale * dl, scale * dm
+    gtd = float((gl * dl).sum() + (gm * dm).sum())
+    t = time.perf_counter()
+    alpha, trials, J1 = 1.0, 0, J0
+    for _ in range(args.large_backtracks):
+        trials += 1
+        try:
+            ctx.set_material((ml + alpha * dl).float().contiguous(), (mm + alpha * dm).float().contiguous())
+            Jt = ctx.misfit(obs, 0, S)
+        except FWIError:  # beyond the time-step limit: a rejected trial
+            Jt = float("inf")
+        if Jt <= J0 + 1e-4 * alpha * gtd:
+            J1 = Jt
+            break
+        alpha *= 0.5
+    else:
+        alpha = 0.0
+    torch.cuda.synchronize()
+    t_ls = time.perf_counter() - t
+    every = math.ceil(math.sqrt(w.nsteps))
+    work = ctx.nelem * 4 * w.nsteps * 2 * S  # forward and adjoint sweeps of the gradient
+    print(json.dumps({
+        "metric": "large autograd inversion iteration", "workload": "large_160x160x80",
+        "mesh": f"{w.nx}x{w.ny}x{w.nz}+{w.npml} PML", "elements": ctx.nelem, "nodes": ctx.nnode, "nsteps": w.nsteps,
+        "shots": S, "shots_of_configuration": w.nshots, "shot_batch": min(S, args.full_batch),
+        "checkpoint": {"interval": every, "snapshots_per_shot": math.ceil(w.nsteps / every), "kind": "compact"},
+        "device_bytes_held": held, "J_start": J0, "J_end": J1, "alpha": alpha, "line_search_trials": trials,
+        "directional_derivative": gtd,
+        "seconds": {"observed_forward": t_obs, "misfit_and_gradient": t_grad, "line_search": t_ls},
+        "element_stage_updates_per_s": work / t_grad,
+        "gradient_seconds_per_shot": t_grad / S,
+        "full_iteration_projected_s": (t_grad + t_ls) * w.nshots / S}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -854,12 +1001,29 @@ def main():
                     help="instead of the headline benchmark: train and evaluate the learned preconditioner")
     ap.add_argument("--study-train", type=int, default=200)
     ap.add_argument("--study-test", type=int, default=20)
-    ap.add_argument("--study-iters", type=int, default=10)
+    ap.add_argument("--study-iters", type=int, default=20)
     ap.add_argument("--study-pair-iters", type=int, default=2)
     ap.add_argument("--study-train-steps", type=int, default=3000)
     ap.add_argument("--study-lr", type=float, default=3e-4)
     ap.add_argument("--study-widths", type=int, nargs=3, default=[28, 56, 112])
+    ap.add_argument("--full-evaluation", action="store_true",
+                    help="instead of the headline benchmark: whole 3000-step 16-shot gradient evaluations of "
+                         "the layered workload (minutes each; --warmup defaults to 0 here)")
+    ap.add_argument("--full-batch", type=int, default=4, help="shot batch of --full-evaluation / --large-iteration")
+    ap.add_argument("--large-iteration", action="store_true",
+                    help="instead of the headline benchmark: one autograd inversion iteration on the "
+                         "160x160x80 + 12 PML workload (4000 steps) over --large-shots shots")
+    ap.add_argument("--large-shots", type=int, default=1)
+    ap.add_argument("--large-backtracks", type=int, default=6)
     args = ap.parse_args()
+    if args.full_evaluation:
+        if "--warmup" not in sys.argv:
+            args.warmup = 0
+        if "--steps" not in sys.argv:
+            args.steps = 1
+        return run_full_evaluation(args)
+    if args.large_iteration:
+        return run_large_iteration(args)
     if args.precond_study:
         return run_precond_study(args)
     if args.precond_bench:

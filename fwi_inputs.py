@@ -148,6 +148,10 @@ def medium(w: Workload, which: str = "true"):
         if which == "true":
             return random_medium(w, w.seed)
         return lame_from_velocities(np.full(shape, 200.0), np.full(shape, 400.0), w.rho)
+    if w.name.startswith("large"):
+        if which == "true":
+            return large_medium(w)
+        return lame_from_velocities(np.full(shape, 200.0), np.full(shape, 400.0), w.rho)
     if w.name.startswith("layered"):
         r = vp_over_vs(0.3)
         Z, Y, X = _grid(w)
@@ -186,6 +190,28 @@ def random_medium(w: Workload, seed: int):
     return lame_from_velocities(vs, vp, w.rho)
 
 
+def large_medium(w: Workload):
+    """(lambda, mu) of the large inversion workload: a Gaussian random field (correlation
+    length 8 m, max |delta| = 0.2 on Vs 200 and Vp 400 m/s) with two sharp ellipsoidal
+    inclusions, a fast one (Vs and Vp of the background x 1.4) in the upper half and a
+    slow one (x 0.7) deeper, their centres jittered by the workload's seed."""
+    rng = np.random.Generator(np.random.PCG64(w.seed))
+    d = gaussian_random_field(w.mat_shape, 8.0 / (0.5 * w.h), int(rng.integers(1 << 30)), 0.2)
+    vs0, vp0 = 200.0 * (1 + d), 400.0 * (1 + d)
+    vs, vp = vs0.copy(), vp0.copy()
+    Z, Y, X = _grid(w)
+    Lx, Ly, Lz = w.nx * w.h, w.ny * w.h, w.nz * w.h
+    for (fx, fy, fz), radii, f in (((0.35, 0.40, 0.35), (14.0, 10.0, 8.0), 1.4),
+                                   ((0.65, 0.60, 0.65), (12.0, 16.0, 9.0), 0.7)):
+        c = ((fx + rng.uniform(-0.05, 0.05)) * Lx, (fy + rng.uniform(-0.05, 0.05)) * Ly,
+             (fz + rng.uniform(-0.05, 0.05)) * Lz)
+        inside = (((X - c[0]) / radii[0]) ** 2 + ((Y - c[1]) / radii[1]) ** 2 +
+                  ((Z - c[2]) / radii[2]) ** 2) <= 1.0
+        vs = np.where(inside, vs0 * f, vs)
+        vp = np.where(inside, vp0 * f, vp)
+    return lame_from_velocities(vs, vp, w.rho)
+
+
 def vp_max(w: Workload):
     lam, mu = medium(w, "true")
     return float(np.sqrt((lam + 2 * mu) / w.rho).max())
@@ -220,6 +246,10 @@ def media_16x16x8(seed=0):
 
 def layered_96x96x48():  # 3 layers + sharp inclusion, 16 shots, 3000 steps, 48x48 receivers
     return build(Workload("layered_96x96x48", 96, 96, 48, 10, 1.0, 3000, 10.0, 48, nshots=16, seed=3))
+
+
+def large_160x160x80():  # GRF + 2 sharp inclusions, 64 shots, 4000 steps, 80x80 receivers
+    return build(Workload("large_160x160x80", 160, 160, 80, 12, 1.0, 4000, 10.0, 80, nshots=64, seed=4))
 
 
 def tiny(nx=3, ny=3, nz=2, npml=2, nsteps=60, f0=25.0, nrec_side=3, seed=5):

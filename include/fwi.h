@@ -62,7 +62,8 @@ typedef enum {
   FWI_E_UNSTABLE = 4,  /* time step above the RK4 stability estimate */
   FWI_E_NONFINITE = 5, /* NaN or Inf in material, traces or gradients */
   FWI_E_TIMEOUT = 6,   /* a bounded device wait gave up */
-  FWI_E_STATE = 7      /* call out of order (e.g. no material or receivers yet) */
+  FWI_E_STATE = 7,     /* call out of order (e.g. no material or receivers yet) */
+  FWI_E_BOUNDS = 8     /* bounds-checked build only: a device index was out of range */
 } fwi_status;
 
 enum { FWI_WAVELET_RICKER = 0, FWI_WAVELET_GAUSS = 1 };
@@ -92,6 +93,16 @@ void fwi_destroy(fwi_ctx *ctx);
 
 /* Last error message of this context (never NULL; "" when none). */
 const char *fwi_last_error(const fwi_ctx *ctx);
+
+/* 1 if this library was compiled with -DFWI_BOUNDS_CHECK, else 0 (host only; no
+ * context, no device work). In that build every node number a kernel reads from a list
+ * (interface shell, outer faces, source and receiver points, snapshot and sweep node
+ * lists) and every node a structured kernel derives from its tile, with the reach of
+ * its stencils, is checked before any access; an index out of range is skipped and
+ * recorded, and the next synchronising call (fwi_forward, fwi_misfit,
+ * fwi_adjoint_gradient, fwi_rhs, fwi_step) returns FWI_E_BOUNDS with the index and the
+ * check site in fwi_last_error(). The results of the two builds are otherwise the same. */
+int fwi_bounds_checked(void);
 
 /* Static description of a status code. */
 const char *fwi_status_string(fwi_status s);

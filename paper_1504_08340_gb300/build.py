@@ -20,18 +20,21 @@ def _nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+CHECK_LIB = os.path.join(HERE, "libfwi_check.so")  # the -DFWI_BOUNDS_CHECK build
+
+
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not _stale():
-        return LIB
-    bdir = os.path.join(HERE, "_build")
+def build(force: bool = False, verbose: bool = False, extra=(), lib=LIB) -> str:
+    if not force and not _stale(lib):
+        return lib
+    bdir = os.path.join(HERE, "_build" if lib == LIB else "_build_" + os.path.basename(lib).split(".")[0])
     os.makedirs(bdir, exist_ok=True)
     common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I", INCLUDE, "-I", CSRC, *extra]
@@ -46,11 +49,19 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The bounds-checked library (every list-derived and tile-derived device index guarded,
+    FWI_E_BOUNDS on a failed check), for tests; load it with FWI_LIBRARY=<path>."""
+    return build(force, verbose, extra=("-DFWI_BOUNDS_CHECK",), lib=CHECK_LIB)
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+    if "--checked" in sys.argv:
+        print(build_checked(force="--force" in sys.argv, verbose=True))

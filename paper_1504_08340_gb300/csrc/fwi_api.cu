@@ -67,8 +67,10 @@ struct fwi_ctx {
   // forward-state checkpointing of the adjoint sweep (fwi_set_checkpointing)
   int ckpt = 0;                 // 0: full displacement history; > 0: snapshot interval; < 0: ceil(sqrt(N))
   float *rstate[4] = {nullptr, nullptr, nullptr, nullptr};  // RK4 state set of the forward recompute
-  float *d_snap = nullptr;      // snapshots of X, [segment][27 * stride]
+  float *d_snap = nullptr;      // compact snapshots of X (snap_floats each), [shot][segment]
   size_t snap_cap = 0;          // snapshots d_snap holds
+  int *d_pml_list = nullptr;    // the PML nodes (nodes of at least one PML element), (k, j, i) order
+  unsigned long long *d_oob = nullptr;  // error word of the bounds-checked build (see fwi::guard)
 
   // reduced-space update (fwi_step): model, gradient, direction, L-BFGS pairs (FP64)
   int lb_cap = 0, lb_count = 0, lb_head = 0;
@@ -169,6 +171,10 @@ void dfree(T *&p) {
 size_t set_floats(const fwi_ctx *c) { return (size_t)fwi::kFields * c->geo.stride; }
 size_t trace_floats(const fwi_ctx *c) { return (size_t)(c->cfg.nsteps + 1) * c->nrec * 3; }
 size_t level_floats(const fwi_ctx *c) { return (size_t)3 * c->geo.nmat; }
+// floats of one shot's compact snapshot: u and udot everywhere, the other 21 fields at the
+// PML nodes (see fwi::launch_snapshot), each PML slot padded to a multiple of 64 floats
+int64_t pml_pad(const fwi_ctx *c) { return (c->npml_nodes + 63) / 64 * 64; }
+size_t snap_floats(const fwi_ctx *c) { return (size_t)6 * c->geo.stride + (size_t)21 * pml_pad(c); }
 
 bool is_dirichlet(const fwi_ctx *c, int i, int j, int k) {
   const int *n = c->geo.n;
@@ -298,8 +304,20 @@ fwi_status time_flush(fwi_ctx *c) {
   return FWI_OK;
 }
 
-// FWI_E_TIMEOUT if a bounded device wait gave up since the last check (synchronises)
+// FWI_E_BOUNDS if a guarded index was out of range (bounds-checked build), FWI_E_TIMEOUT
+// if a bounded device wait gave up, since the last check (synchronises)
 fwi_status check_status(fwi_ctx *c) {
+  if (c->d_oob) {
+    unsigned long long w = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&w, c->d_oob, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (w != 0) {
+      CUDA_TRY(c, cudaMemsetAsync(c->d_oob, 0, sizeof(w), c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      return fail(c, FWI_E_BOUNDS, "index %lld out of range at check site %d", (long long)(w & 0xffffffffffffull),
+                  (int)(w >> 48));
+    }
+  }
   if (!c->d_status) return FWI_OK;
   int st = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -371,6 +389,8 @@ fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot0, int nb, float *hist_
     a.hstride = hstride;
     TRY(stage(c, adj, a));
     fwi::PointArgs p{};
+    p.nnode_pad = (int64_t)c->geo.px * c->geo.n[1] * c->geo.n[2];
+    p.oob = c->geo.oob;
     p.buf = outs[s];
     p.stride = c->geo.stride;
     p.cdt = cdt[s];
@@ -422,6 +442,50 @@ fwi_status ensure_trace_buffers(fwi_ctx *c) {
   return FWI_OK;
 }
 
+// the PML node list of the compact snapshots, built on first use
+fwi_status ensure_pml_list(fwi_ctx *c) {
+  if (c->d_pml_list) return FWI_OK;
+  const fwi::Geo &g = c->geo;
+  std::vector<char> all_rd[3];  // per axis: every element along it around the coordinate is interior
+  for (int ax = 0; ax < 3; ax++) {
+    all_rd[ax].assign(g.n[ax], 0);
+    for (int cc = 0; cc < g.n[ax]; cc++) {
+      bool all = true;
+      if (cc & 1) {
+        const int e = (cc - 1) / 2;
+        all = e >= g.lo[ax] && e < g.hi[ax];
+      } else {
+        if (cc >= 2) all = all && (cc / 2 - 1 >= g.lo[ax] && cc / 2 - 1 < g.hi[ax]);
+        if (cc <= g.n[ax] - 3) all = all && (cc / 2 >= g.lo[ax] && cc / 2 < g.hi[ax]);
+      }
+      all_rd[ax][cc] = all;
+    }
+  }
+  std::vector<int> list;
+  list.reserve((size_t)c->npml_nodes);
+  for (int k = 0; k < g.n[2]; k++)
+    for (int j = 0; j < g.n[1]; j++)
+      for (int i = 0; i < g.n[0]; i++)
+        if (!(all_rd[0][i] && all_rd[1][j] && all_rd[2][k])) list.push_back((k * g.n[1] + j) * g.px + i);
+  if ((int64_t)list.size() != c->npml_nodes) return fail(c, FWI_E_CUDA, "PML node list size mismatch");
+  if (list.empty()) list.push_back(0);  // a PML-free box: slots of zero length, one valid entry
+  TRY(dalloc(c, &c->d_pml_list, list.size()));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_pml_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FWI_OK;
+}
+
+// compact snapshot g of the nb step-start states X (shot b's at (b * nseg + g) * snap_floats)
+fwi_status take_snapshot(fwi_ctx *c, float *snap, int g, int nseg, int nb) {
+  const size_t sf = snap_floats(c);
+  fwi::launch_snapshot(c->state[0], snap + (size_t)g * sf, c->d_pml_list, c->npml_nodes, pml_pad(c), c->geo.stride,
+                       nb, (int64_t)set_floats(c), (int64_t)(nseg * sf), true, c->stream, c->geo.oob);
+  c->t_launch[3]++;
+  CUDA_TRY(c, cudaGetLastError());
+  return FWI_OK;
+}
+
 // forward sweep of shots shot0 .. shot0 + nb - 1 into d_traces (shot b at b * trace_floats);
 // hist: optional displacement history (shot b at b * hstride); snap: optional snapshots of
 // the step-start state X every `every` steps (shot b's segment g at (b * nseg + g) * set)
@@ -436,7 +500,7 @@ fwi_status forward_sweep_body(fwi_ctx *c, int shot0, int nb, float *hist, int64_
     for (int b = 0; b < nb; b++)
       CUDA_TRY(c, cudaMemsetAsync(hist + b * hstride, 0, sizeof(float) * hstep, c->stream));
   fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces, c->stream, nb,
-                     (int64_t)sfloats, tf);
+                     (int64_t)sfloats, tf, c->geo.oob);
   if (c->persistent) {
     if (!c->d_rec_of) {
       std::vector<int> rec_of((size_t)c->geo.stride, -1);
@@ -470,10 +534,7 @@ fwi_status forward_sweep_body(fwi_ctx *c, int shot0, int nb, float *hist, int64_
     p.status = c->d_status;
     const int seg = snap ? every : c->cfg.nsteps;
     for (int n0 = 0; n0 < c->cfg.nsteps; n0 += seg) {
-      if (snap)
-        for (int b = 0; b < nb; b++)
-          CUDA_TRY(c, cudaMemcpyAsync(snap + ((size_t)b * nseg + n0 / every) * sfloats, c->state[0] + b * sfloats,
-                                      sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+      if (snap) TRY(take_snapshot(c, snap, n0 / every, nseg, nb));
       p.n0 = n0;
       p.n1 = std::min(n0 + seg, c->cfg.nsteps);
       CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream));
@@ -484,13 +545,10 @@ fwi_status forward_sweep_body(fwi_ctx *c, int shot0, int nb, float *hist, int64_
     return FWI_OK;
   }
   for (int n = 0; n < c->cfg.nsteps; n++) {
-    if (snap && n % every == 0)
-      for (int b = 0; b < nb; b++)
-        CUDA_TRY(c, cudaMemcpyAsync(snap + ((size_t)b * nseg + n / every) * sfloats, c->state[0] + b * sfloats,
-                                    sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (snap && n % every == 0) TRY(take_snapshot(c, snap, n / every, nseg, nb));
     TRY(rk4_step(c, false, n, shot0, nb, hist ? hist + (size_t)(n + 1) * hstep : nullptr, hstride));
     fwi::launch_sample(c->state[0], c->geo.stride, c->nrec, c->d_rec_node, c->d_traces + (n + 1) * per_step,
-                       c->stream, nb, (int64_t)sfloats, tf);
+                       c->stream, nb, (int64_t)sfloats, tf, c->geo.oob);
     c->t_launch[2]++;
     c->t_launch[3]++;
   }
@@ -570,11 +628,20 @@ const char *fwi_status_string(fwi_status s) {
     case FWI_E_NONFINITE: return "non-finite value";
     case FWI_E_TIMEOUT: return "bounded device wait gave up";
     case FWI_E_STATE: return "call out of order";
+    case FWI_E_BOUNDS: return "device index out of range";
   }
   return "unknown status";
 }
 
 const char *fwi_last_error(const fwi_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int fwi_bounds_checked(void) {
+#ifdef FWI_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   if (!cfg || !out) return FWI_E_INVAL;
@@ -737,6 +804,12 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
   if (st == FWI_OK) st = dalloc(c, &c->d_mu, (size_t)g.nmat);
   if (st == FWI_OK) st = dalloc(c, &c->d_lam_n, (size_t)g.stride);
   if (st == FWI_OK) st = dalloc(c, &c->d_mu_n, (size_t)g.stride);
+#ifdef FWI_BOUNDS_CHECK
+  if (st == FWI_OK) st = dalloc(c, &c->d_oob, 1);
+  if (st == FWI_OK && cudaMemset(c->d_oob, 0, sizeof(unsigned long long)) != cudaSuccess)
+    st = fail(c, FWI_E_CUDA, "error word clear failed");
+#endif
+  g.oob = c->d_oob;
   if (st == FWI_OK) {
     g.lam = c->d_lam;
     g.mu = c->d_mu;
@@ -773,6 +846,8 @@ void fwi_destroy(fwi_ctx *c) {
   dfree(c->d_mu_n);
   drop_graphs(c);
   dfree(c->d_all);
+  dfree(c->d_pml_list);
+  dfree(c->d_oob);
   dfree(c->d_rec_of);
   dfree(c->d_bar);
   dfree(c->d_status);
@@ -1033,11 +1108,12 @@ fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed
   const int64_t hstride = (int64_t)(slots * hstep);  // one shot's history levels
   TRY(ensure_hist(c, slots));
   if (every > 0) {
+    TRY(ensure_pml_list(c));
     const size_t nsnap = (size_t)nseg * c->batch;
     if (c->snap_cap < nsnap) {
       dfree(c->d_snap);
       c->snap_cap = 0;
-      TRY(dalloc(c, &c->d_snap, nsnap * sfloats));
+      TRY(dalloc(c, &c->d_snap, nsnap * snap_floats(c)));
       c->snap_cap = nsnap;
     }
     for (int b = 0; b < 4; b++) {
@@ -1083,10 +1159,12 @@ fwi_status run_gradient(fwi_ctx *c, int shot0, int nshots, const float *observed
         const int L0 = g * every, L1 = std::min(L0 + every, N);
         std::swap(c->state, c->rstate);
         fwi_status rs = FWI_OK;
-        for (int b = 0; b < nb && rs == FWI_OK; b++)
-          if (cudaMemcpyAsync(c->state[0] + b * sfloats, c->d_snap + ((size_t)b * nseg + g) * sfloats,
-                              sfloats * sizeof(float), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-            rs = fail(c, FWI_E_CUDA, "snapshot restore failed");
+        const size_t sf = snap_floats(c);
+        fwi::launch_snapshot(c->state[0], c->d_snap + (size_t)g * sf, c->d_pml_list, c->npml_nodes, pml_pad(c),
+                             c->geo.stride, nb, (int64_t)sfloats, (int64_t)(nseg * sf), false, c->stream,
+                             c->geo.oob);
+        c->t_launch[3]++;
+        if (cudaGetLastError() != cudaSuccess) rs = fail(c, FWI_E_CUDA, "snapshot restore failed");
         for (int n = L0; n < L1 && rs == FWI_OK; n++)
           rs = rk4_step(c, false, n, shot0 + s0, nb, c->d_hist + (size_t)(n + 1 - L0) * hstep, hstride);
         std::swap(c->state, c->rstate);
@@ -1438,7 +1516,7 @@ fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int
     CUDA_TRY(c, cudaMemsetAsync(c->state[2], 0, n * sizeof(float), c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
-  return FWI_OK;
+  return check_status(c);
 }
 
 fwi_status fwi_get_state(fwi_ctx *c, float *state, int on_device) {
@@ -1522,7 +1600,8 @@ size_t bytes_per_shot(const fwi_ctx *c) {
   if (every == 0)
     f += (size_t)(N + 1) * level_floats(c);
   else
-    f += (size_t)(every + 1) * level_floats(c) + (size_t)((N + every - 1) / every + 4) * set_floats(c);
+    f += (size_t)(every + 1) * level_floats(c) + (size_t)((N + every - 1) / every) * snap_floats(c) +
+         (size_t)4 * set_floats(c);
   return f * sizeof(float);
 }
 
@@ -1545,7 +1624,7 @@ fwi_status fwi_tune_shot_batch(fwi_ctx *c, int shot0, int nshots, int max_batch,
   // memory cap: what is free plus what this context's per-shot buffers hold now
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
-  size_t held = (size_t)4 * set_floats(c) * c->batch + c->hist_cap * level_floats(c) + c->snap_cap * set_floats(c);
+  size_t held = (size_t)4 * set_floats(c) * c->batch + c->hist_cap * level_floats(c) + c->snap_cap * snap_floats(c);
   if (c->rstate[0]) held += (size_t)4 * set_floats(c) * c->batch;
   if (c->d_traces) held += (size_t)3 * trace_floats(c) * c->batch;
   held *= sizeof(float);

@@ -210,6 +210,7 @@ __device__ __forceinline__ void finish_node(const Geo &g, const StageArgs &a, in
   const int64_t S = g.stride;
   const int64_t node = ((int64_t)K * g.n[1] + J) * g.px + I;
   const int64_t mi = ((int64_t)(K - 2 * g.lo[2]) * g.m[1] + (J - 2 * g.lo[1])) * g.m[0] + (I - 2 * g.lo[0]);
+  if (!guard(g.oob, kSiteInterior, mi, g.nmat)) return;
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     const int64_t i1 = (int64_t)(9 + c) * S + node, i2 = (int64_t)(18 + c) * S + node;
@@ -289,17 +290,19 @@ __global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g,
     t.ms2 = g.m[0] * g.m[1];
     t.mi = ((K - 2 * g.lo[2]) * g.m[1] + (J - 2 * g.lo[1])) * g.m[0] + (IE - 2 * g.lo[0]);
     const int64_t rowbase = ((int64_t)K * g.n[1] + J) * g.px;
+    const bool e_ok = even_ok && node_ok(g, kSiteInterior, rowbase + IE);
+    const bool o_ok = odd_ok && node_ok(g, kSiteInterior, rowbase + IO);
     Own oe, oo;
-    if (even_ok) load_own(g, a, rowbase + IE, oe);
-    if (odd_ok) load_own(g, a, rowbase + IO, oo);
-    if (even_ok) {
+    if (e_ok) load_own(g, a, rowbase + IE, oe);
+    if (o_ok) load_own(g, a, rowbase + IO, oo);
+    if (e_ok) {
       float acc[3];
       node_accel_dispatch<kEven>(t, sy, sz, sc, acc);
       finish_node(g, a, IE, J, K, t, oe, acc);
     }
     t.o += 1;
     t.mi += 1;
-    if (odd_ok) {
+    if (o_ok) {
       float acc[3];
       node_accel_dispatch<kOdd>(t, sy, sz, sc, acc);
       finish_node(g, a, IO, J, K, t, oo, acc);

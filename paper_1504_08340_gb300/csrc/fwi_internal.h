@@ -11,6 +11,27 @@ constexpr int kFields = 27;  // 3 levels x (3 displacement + 6 stress components
 constexpr int kLevelFields = 9;
 
 // Mesh geometry and per-node coefficient sources, passed by value to kernels.
+// ---- bounds-checked build (-DFWI_BOUNDS_CHECK)
+// Every node number read from a list (shell, face, source and receiver points, snapshot
+// and sweep lists) and every node a structured kernel derives from its tile is checked
+// before any access: a failed check records (site << 48) | (index & (2^48 - 1)) in the
+// context's error word (the first one wins) and the thread skips that node, so nothing out
+// of range is read or written; the call then returns FWI_E_BOUNDS. In the normal build
+// guard() is the constant true and the checks compile away.
+enum BoundsSite {
+  kSiteShell = 1, kSiteFace = 2, kSitePml = 3, kSiteInterior = 4, kSitePoint = 5, kSiteSample = 6,
+  kSiteGradient = 7, kSiteSnapshot = 8, kSitePersist = 9
+};
+#ifdef FWI_BOUNDS_CHECK
+__device__ __forceinline__ bool guard(unsigned long long *err, int site, long long idx, long long n) {
+  if (idx >= 0 && idx < n) return true;
+  if (err) atomicCAS(err, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)idx & 0xffffffffffffull));
+  return false;
+}
+#else
+__device__ __forceinline__ bool guard(unsigned long long *, int, long long, long long) { return true; }
+#endif
+
 struct Geo {
   int n[3];         // nodes per axis (NI, NJ, NK)
   int px;           // row pitch: node (i, j, k) is at (k * NJ + j) * px + i; px = NI rounded up to 4
@@ -33,6 +54,7 @@ struct Geo {
   int nshell;
   const int *face;        // node numbers of the PML nodes on the grid's outer faces
   int nface;
+  unsigned long long *oob;  // error word of the bounds-checked build (else null)
   // launch shapes (fwi_tune_tiles; they change no node's arithmetic)
   int int_kc;             // planes per block of interior_kernel
   int pml_seg;            // node pairs per x segment of a pml_kernel warp task (<= 32)
@@ -66,6 +88,11 @@ __host__ __device__ inline StageArgs shot_args(StageArgs a, int shot) {
   a.out += o;
   if (a.hist) a.hist += (int64_t)shot * a.hstride;
   return a;
+}
+
+// a node number of the state layout: inside the grid and not in a row's padding
+__device__ __forceinline__ bool node_ok(const Geo &g, int site, long long node) {
+  return guard(g.oob, site, node, (long long)g.px * g.n[1] * g.n[2]) && guard(g.oob, site, node % g.px, g.n[0]);
 }
 
 // One RK4 stage is five kernels writing disjoint node sets; they read the same
@@ -132,13 +159,16 @@ struct PointArgs {
   // receivers: its residuals start at table + b * tstride
   int nshot;
   int64_t sstride, tstride;
+  int64_t nnode_pad;          // valid node numbers: [0, nnode_pad) (bounds-checked build)
+  unsigned long long *oob;    // error word of the bounds-checked build (else null)
 };
 void launch_point(const PointArgs &p, cudaStream_t s);
 
 // traces[b][r][c] = buf[b * sstride + (9 + c) * stride + node[r]] for the nshot shots of a
 // batch (trace of shot b at traces + b * tstride)
 void launch_sample(const float *buf, int64_t stride, int nrec, const int64_t *node, float *traces,
-                   cudaStream_t s, int nshot = 1, int64_t sstride = 0, int64_t tstride = 0);
+                   cudaStream_t s, int nshot = 1, int64_t sstride = 0, int64_t tstride = 0,
+                   unsigned long long *oob = nullptr);
 
 // Gradient integrand of (C.1f)/(C.1g) at one time level, accumulated in FP64:
 // gl[i] -= wdt * sum_e W detJ (div w)(div u), gm[i] -= wdt * sum_e W detJ 2 eps(w):eps(u),
@@ -153,6 +183,15 @@ int misfit_blocks(int64_t n);
 void launch_residual(const float *traces, const float *observed, float *resid, int64_t n,
                      int64_t per_step, int nsteps, double dt, double *part, int *flag, cudaStream_t s);
 void launch_sum(const double *part, int nblocks, double *out, cudaStream_t s);
+
+// Compact snapshot of nshot RK4 state sets (shot b at state + b sstride) into snap (shot b
+// at snap + b snap_stride), or back (pack = false): u and udot (fields 9-11, 18-20) over
+// all `stride` entries, then the other 21 fields at the npml PML nodes of `list`, each in
+// a slot of npad >= npml floats (npad a multiple of 64). The restored state's other
+// entries of those 21 fields must already be zero (no stage kernel writes them).
+void launch_snapshot(float *state, float *snap, const int *list, int64_t npml, int64_t npad, int64_t stride,
+                     int nshot, int64_t sstride, int64_t snap_stride, bool pack, cudaStream_t s,
+                     unsigned long long *oob = nullptr);
 
 // flag = 1 if any value of x (n doubles) is not finite.
 void launch_check_finite(const double *x, int64_t n, int *flag, cudaStream_t s);

@@ -23,6 +23,7 @@ __global__ void point_kernel(PointArgs p) {
   const int b = t / p.npts, i = t - b * p.npts;  // shot of the batch, point
   const int k = p.mode == 0 ? b : i;             // sources: one point per shot
   const int64_t n = p.node[k];
+  if (!guard(p.oob, kSitePoint, n, p.nnode_pad)) return;
   float *buf = p.buf + (int64_t)b * p.sstride;
   const float *table = p.mode == 0 ? p.table : p.table + (int64_t)b * p.tstride;
   for (int c = 0; c < 3; c++) {
@@ -39,12 +40,14 @@ __global__ void point_kernel(PointArgs p) {
 }
 
 __global__ void sample_kernel(const float *buf, int64_t stride, int nrec, const int64_t *node, float *tr,
-                              int nshot, int64_t sstride, int64_t tstride) {
+                              int nshot, int64_t sstride, int64_t tstride, unsigned long long *oob) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nrec * 3 * nshot) return;
   const int b = t / (nrec * 3), i = t - b * nrec * 3;
   const int r = i / 3, c = i % 3;
-  tr[(int64_t)b * tstride + i] = buf[(int64_t)b * sstride + (int64_t)(9 + c) * stride + node[r]];
+  const int64_t n = node[r];
+  if (!guard(oob, kSiteSample, n, stride)) return;
+  tr[(int64_t)b * tstride + i] = buf[(int64_t)b * sstride + (int64_t)(9 + c) * stride + n];
 }
 
 // (C.1f)/(C.1g) at one time level, in FP64: for every interior node, the sum over the
@@ -166,8 +169,10 @@ __global__ void __launch_bounds__(kGX *kGY, 3) gradient_kernel(Geo g, const floa
             }
         const float W = Wxy * (oz ? 4.f / 3.f : 1.f / 3.f);
         const int64_t mi = ((int64_t)k * g.m[1] + j) * g.m[0] + i;
-        gl[mi] -= wdt * (double)W * (double)sl;
-        gm[mi] -= wdt * (double)W * (double)smu;
+        if (guard(g.oob, kSiteGradient, mi, g.nmat)) {
+          gl[mi] -= wdt * (double)W * (double)sl;
+          gm[mi] -= wdt * (double)W * (double)smu;
+        }
       }
       cp_async_wait_all();
       __syncthreads();
@@ -230,10 +235,10 @@ void launch_point(const PointArgs &p, cudaStream_t s) {
 }
 
 void launch_sample(const float *buf, int64_t stride, int nrec, const int64_t *node, float *traces,
-                   cudaStream_t s, int nshot, int64_t sstride, int64_t tstride) {
+                   cudaStream_t s, int nshot, int64_t sstride, int64_t tstride, unsigned long long *oob) {
   if (nrec <= 0 || nshot <= 0) return;
   sample_kernel<<<blocks_for((int64_t)nrec * 3 * nshot, 256), 256, 0, s>>>(buf, stride, nrec, node, traces, nshot,
-                                                                           sstride, tstride);
+                                                                           sstride, tstride, oob);
 }
 
 void launch_gradient(const Geo &g, const float *w_state, const float *u_hist, double wdt, double *gl,
@@ -293,6 +298,55 @@ void launch_extend_material(const Geo &g, float *lam_n, float *mu_n, cudaStream_
   const int64_t n = (int64_t)g.px * g.n[1] * g.n[2];
   int64_t b = (n + 255) / 256;
   extend_material_kernel<<<(int)(b > 4096 ? 4096 : b), 256, 0, s>>>(g, lam_n, mu_n);
+}
+
+// ---- compact forward-state snapshots (checkpointed adjoint sweep)
+// Slots 0..5 hold the fields 9, 10, 11, 18, 19, 20 (u and udot) of every entry; slots
+// 6..26 hold the other 21 fields (ubar and the three stress levels) at the PML nodes of
+// `list` only, npad values each: those fields are zero at every other entry of any state.
+namespace {
+__device__ __forceinline__ int snap_field(int slot) {
+  if (slot < 3) return 9 + slot;
+  if (slot < 6) return 15 + slot;              // 18, 19, 20
+  const int k = slot - 6;                      // 0..20
+  return k < 9 ? k : (k < 15 ? k + 3 : k + 6);  // 0..8, 12..17, 21..26
+}
+
+template <bool PACK>
+__global__ void __launch_bounds__(256) snapshot_kernel(float *state, float *snap, const int *__restrict__ list,
+                                                       int64_t npml, int64_t npad, int64_t stride, int64_t sstride,
+                                                       int64_t snap_stride, unsigned long long *oob) {
+  const int slot = blockIdx.y;
+  float *st = state + (int64_t)blockIdx.z * sstride + (int64_t)snap_field(slot) * stride;
+  float *sn = snap + (int64_t)blockIdx.z * snap_stride;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, dt = (int64_t)gridDim.x * blockDim.x;
+  if (slot < 6) {  // dense: stride is a multiple of 64 floats and every base is 256-byte aligned
+    float4 *a = reinterpret_cast<float4 *>(sn + (int64_t)slot * stride);
+    float4 *b = reinterpret_cast<float4 *>(st);
+    for (int64_t i = t0; i < stride / 4; i += dt) {
+      if (PACK) __stcs(a + i, __ldcs(b + i));
+      else __stcs(b + i, __ldcs(a + i));
+    }
+  } else {
+    float *a = sn + 6 * stride + (int64_t)(slot - 6) * npad;
+    for (int64_t p = t0; p < npml; p += dt) {
+      const int64_t n = __ldg(list + p);
+      if (!guard(oob, kSiteSnapshot, n, stride)) continue;
+      if (PACK) __stcs(a + p, __ldcs(st + n));
+      else __stcs(st + n, __ldcs(a + p));
+    }
+  }
+}
+}  // namespace
+
+void launch_snapshot(float *state, float *snap, const int *list, int64_t npml, int64_t npad, int64_t stride,
+                     int nshot, int64_t sstride, int64_t snap_stride, bool pack, cudaStream_t s,
+                     unsigned long long *oob) {
+  const dim3 grid(296, 27, nshot);
+  if (pack)
+    snapshot_kernel<true><<<grid, 256, 0, s>>>(state, snap, list, npml, npad, stride, sstride, snap_stride, oob);
+  else
+    snapshot_kernel<false><<<grid, 256, 0, s>>>(state, snap, list, npml, npad, stride, sstride, snap_stride, oob);
 }
 
 void launch_check_finite(const double *x, int64_t n, int *flag, cudaStream_t s) {

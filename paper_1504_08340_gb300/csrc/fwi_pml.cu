@@ -555,6 +555,14 @@ __global__ void __launch_bounds__(kBX *kBY, PART == 0 ? FWI_PML_MINB : FWI_PML_S
   const int p = R > 1 ? threadIdx.x % P : threadIdx.x;  // pair of the segment (P <= 32)
   if (p < P) {
     const int I0 = x0 + 2 * (pb + p);
+    // reach of the pair's stencils: the x window I0-2 .. I0+3 of its row, +-1 (odd) or
+    // +-2 (even) rows and planes
+    const int ry = ky == kSC ? 1 : 2, rz = kz == kSC ? 1 : 2;
+    if (!(guard(g.oob, kSitePml, J - ry, g.n[1]) && guard(g.oob, kSitePml, J + ry, g.n[1]) &&
+          guard(g.oob, kSitePml, K - rz, g.n[2]) && guard(g.oob, kSitePml, K + rz, g.n[2]) &&
+          guard(g.oob, kSitePml, I0 + 3, g.px) &&
+          guard(g.oob, kSitePml, ((long long)K * g.n[1] + J) * g.px + I0 - 2, (long long)g.px * g.n[1] * g.n[2])))
+      return;
     // box x-ranges end at odd nodes, so the odd node of a pair is always in the box;
     // the even node of a box's first pair may not be (its results are dropped)
     const bool even_ok = I0 >= r.lo[b][0];
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(3 * kFaceNodes, FWI_FACE_MINB) pml_face_kernel
   const StageArgs a = shot_args(a0, blockIdx.x / nbs);
   const int lane = threadIdx.x, w = threadIdx.y;
   const int i = (blockIdx.x % nbs) * kFaceNodes + lane;
-  const bool live = i < g.nface;
+  const bool live = i < g.nface && node_ok(g, kSiteFace, g.face[i]);
   int I = 0, J = 0, K = 0;
   FaceCtx n;
   if (live) {

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(3 * kShellNodes, FWI_SHELL_MINB) shell_kernel(
   const StageArgs a = shot_args(a0, blockIdx.x / nbs);
   const int lane = threadIdx.x, w = threadIdx.y;
   const int i = (blockIdx.x % nbs) * kShellNodes + lane;
-  const bool live = i < g.nshell;
+  const bool live = i < g.nshell && node_ok(g, kSiteShell, g.shell[i]);
   NodeCtx n;
   if (live) {
     const int node = g.shell[i];
@@ -497,7 +497,7 @@ __device__ __forceinline__ void persist_disp(const Geo &g, const StageArgs &a, c
   if (a.hist) write_hist(g, a, n.c3[0], n.c3[1], n.c3[2], c, v1);
   if (stage == 3) {
     const int r = p.rec_of[n.node];
-    if (r >= 0) p.traces[(int64_t)b * p.tstride + ((int64_t)(step + 1) * p.nrec + r) * 3 + c] = v1;
+    if (r >= 0 && guard(g.oob, kSitePersist, r, p.nrec)) p.traces[(int64_t)b * p.tstride + ((int64_t)(step + 1) * p.nrec + r) * 3 + c] = v1;
   }
 }
 
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(3 * kShellNodes) persistent_forward_kernel(Geo
         const int b = ch / nch;
         const StageArgs a = shot_args(a0, b);
         const int i = (ch % nch) * kShellNodes + lane;
-        const bool live = i < p.nall;
+        const bool live = i < p.nall && node_ok(g, kSitePersist, p.nodes[i]);
         NodeCtx n;
         if (live) {
           const int node = p.nodes[i];

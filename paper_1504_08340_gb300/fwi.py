@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfwi.so")
 
 STATUS = {0: "FWI_OK", 1: "FWI_E_INVAL", 2: "FWI_E_NOMEM", 3: "FWI_E_CUDA", 4: "FWI_E_UNSTABLE",
-          5: "FWI_E_NONFINITE", 6: "FWI_E_TIMEOUT", 7: "FWI_E_STATE"}
+          5: "FWI_E_NONFINITE", 6: "FWI_E_TIMEOUT", 7: "FWI_E_STATE", 8: "FWI_E_BOUNDS"}
 WAVELETS = {"ricker": 0, "gauss": 1}
 
 
@@ -48,7 +48,7 @@ class StepInfo(C.Structure):
 
 
 # every symbol the header declares; the CPU test checks the library exports them all
-EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_get_dims",
+EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_bounds_checked", "fwi_get_dims",
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
            "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_get_state", "fwi_set_graphs", "fwi_set_persistent", "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
@@ -63,11 +63,14 @@ EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "
 _lib = None
 
 
-def load_library(path: str = LIB_PATH):
-    """Load libfwi.so; raises ImportError when it has not been built."""
+def load_library(path: str = None):
+    """Load libfwi.so (or the library FWI_LIBRARY names, e.g. the bounds-checked build
+    libfwi_check.so); raises ImportError when it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("FWI_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with paper_1504_08340_gb300.build.build() "
                           "(or __graft_entry__.build()); there is no CPU fallback")
@@ -78,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_destroy.argtypes = [P]
     lib.fwi_destroy.restype = None
     lib.fwi_last_error.argtypes = [P]
+    lib.fwi_bounds_checked.argtypes = []
     lib.fwi_last_error.restype = C.c_char_p
     lib.fwi_status_string.argtypes = [I]
     lib.fwi_status_string.restype = C.c_char_p
@@ -125,6 +129,11 @@ def load_library(path: str = LIB_PATH):
     lib.fwi_nn_conv3d_backward_weight_work.restype = L
     _lib = lib
     return lib
+
+
+def bounds_checked() -> bool:
+    """True when the loaded library is the -DFWI_BOUNDS_CHECK build (fwi_bounds_checked)."""
+    return bool(load_library().fwi_bounds_checked())
 
 
 def _is_torch(x):

@@ -48,8 +48,19 @@ def test_status_strings():
 
     lib = ctypes.CDLL(b.build())
     lib.fwi_status_string.restype = ctypes.c_char_p
-    for code in range(8):
-        assert lib.fwi_status_string(code)
+    for code in range(9):
+        assert lib.fwi_status_string(code).decode() != "unknown status", code
+
+
+def test_bounds_checked_build_reports_itself():
+    """The -DFWI_BOUNDS_CHECK variant builds, exports the same symbols and says so through
+    fwi_bounds_checked; the normal build says it is not checked (host-only call)."""
+    from paper_1504_08340_gb300 import build as b
+
+    plain, checked = ctypes.CDLL(b.build()), ctypes.CDLL(b.build_checked())
+    assert plain.fwi_bounds_checked() == 0 and checked.fwi_bounds_checked() == 1
+    for name in _declared():
+        assert hasattr(checked, name), name
 
 
 def test_null_context_is_rejected_without_touching_the_gpu():
@@ -96,7 +107,7 @@ def test_null_context_is_rejected_without_touching_the_gpu():
         assert getattr(lib, name)(*args) == inval, name
     # argument checks of the allocation-free misfit come before any device work too
     assert lib.fwi_trace_misfit_noalloc(nul, nul, 10, 4, 1e-3, nul, nul) == inval
-    assert set(calls) | {"fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string",
+    assert set(calls) | {"fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_bounds_checked",
                          "fwi_trace_misfit_noalloc"} == {e for e in fwi.EXPORTS if not e.startswith("fwi_nn_")}
     # the preconditioner kernels check pointers and sizes before any device work
     one = C.c_void_p(1)

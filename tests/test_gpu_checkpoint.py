@@ -1,7 +1,7 @@
 """sqrt(T) checkpointing of the adjoint sweep and the torch.autograd wrapper.
 
-Checkpointing recomputes the forward steps of each segment from a snapshot, so the
-displacement history, and hence J and the gradients, must equal the stored-history
+Checkpointing recomputes the forward steps of each segment from a compact snapshot, so
+the displacement history, and hence J and the gradients, must equal the stored-history
 path bit for bit. The autograd wrapper must hand back exactly what
 fwi_adjoint_gradient returns, and the gradient must match the FP64 oracle."""
 import numpy as np
@@ -47,6 +47,35 @@ def test_checkpointed_gradient_is_bit_identical(nsteps):
         ctx.set_checkpointing(0)
         J, gl, gm = ctx.adjoint_gradient(obs)
         assert J == J0 and torch.equal(gl, gl0) and torch.equal(gm, gm0)
+
+
+@pytest.mark.parametrize("npml,top", [(2, False), (2, True), (0, False)])
+def test_compact_snapshots_batched_bit_identical(npml, top):
+    """Snapshots keep u and udot everywhere and the other 21 fields on the PML nodes only;
+    restoring them must give the stored-history gradients bit for bit for a batch of two
+    with a ragged last group (three shots), with a top PML and on a PML-free box."""
+    from paper_1504_08340_gb300 import Context
+
+    w = fi.tiny(nx=4, ny=3, nz=2, npml=npml, nsteps=41, f0=30.0, nrec_side=3)
+    p, kz = npml, (2 * npml if top else 0)  # the interior's top surface
+    src = np.array([(2 * p + 2, 2 * p + 2, kz), (2 * p + 4, 2 * p + 3, kz), (2 * p + 6, 2 * p + 4, kz)])
+    rec = np.array([(2 * p + i, 2 * p + j, kz) for j in (1, 3, 5) for i in (1, 4, 7)])
+    dirs = np.tile([0.0, 0.0, 1.0], (3, 1))
+    obs = torch.tensor(np.stack([fi.synthetic_traces(w.nsteps, len(rec), 40 + s, scale=1e-7) for s in range(3)]),
+                       dtype=torch.float32, device="cuda").contiguous()
+    with Context(w.nx, w.ny, w.nz, w.npml, w.h, w.dt, w.nsteps, rho=w.rho, top_pml=top) as ctx:
+        l0, m0 = (_f32(a) for a in fi.medium(w, "trial"))
+        ctx.set_material(l0, m0)
+        ctx.set_sources(src, dirs, "ricker", w.ricker())
+        ctx.set_receivers(rec)
+        ctx.set_shot_batch(2)
+        J0, gl0, gm0 = ctx.adjoint_gradient(obs, 0, 3)
+        assert J0 > 0 and float(gl0.abs().max()) > 0
+        for every in (1, 5, -1, 40):
+            ctx.set_checkpointing(every)
+            J, gl, gm = ctx.adjoint_gradient(obs, 0, 3)
+            assert J == J0, every
+            assert torch.equal(gl, gl0) and torch.equal(gm, gm0), every
 
 
 def test_autograd_returns_the_adjoint_gradient(oracle_mod):

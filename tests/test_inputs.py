@@ -102,3 +102,28 @@ def test_random_media_of_the_preconditioner_study():
         assert 0.5 * 0.5 * w.h / w.dt >= vmax
     vs0, vp0 = _velocities(fi.media_16x16x8(0), "trial")
     assert np.all(vs0 == 200.0) and np.all(vp0 == 400.0)
+
+
+def test_large_workload_sizes_and_medium():
+    """The large autograd workload: 160x160x80 interior + 12-element PML (3.11 M elements,
+    25.2 M nodes), 64 shots on an 8x8 surface grid, 80x80 receivers, 4000 steps; a random
+    field of +-20 % about Vs 200 / Vp 400 m/s with a fast (x1.4) and a slow (x0.7) sharp
+    inclusion, and the Courant-0.5 step of its fastest P velocity."""
+    w = fi.large_160x160x80()
+    assert (w.nx, w.ny, w.nz, w.npml, w.nsteps, w.f0, w.nshots) == (160, 160, 80, 12, 4000, 10.0, 64)
+    assert tuple(w.nodes) == (369, 369, 185) and int(np.prod(w.nodes)) == 25_189_785 and int(np.prod(w.mat_shape)) == 16_589_601
+    assert int(np.prod(w.elements)) == 3_114_752
+    src, rec = w.sources(), w.receivers()
+    assert len({tuple(s) for s in src}) == 64 and len(np.unique(src[:, 0])) == 8 and len(np.unique(src[:, 1])) == 8
+    assert len({tuple(r) for r in rec}) == 6400 and np.all(src[:, 2] == 0) and np.all(rec[:, 2] == 0)
+    vs, vp = _velocities(w, "true")
+    assert np.allclose(vp / vs, 2.0)
+    # only the fast inclusion exceeds the field's +20 %, only the slow one falls below -20 %
+    fast, slow = vs > 200 * 1.2 * (1 + 1e-9), vs < 200 * 0.8 * (1 - 1e-9)
+    assert fast.mean() > 1e-3 and slow.mean() > 1e-3
+    assert vs.max() <= 200 * 1.2 * 1.4 * (1 + 1e-9) and vs.min() >= 200 * 0.8 * 0.7 * (1 - 1e-9)
+    Z, Y, X = (a.ravel() for a in np.meshgrid(*[np.arange(n) * 0.5 for n in w.mat_shape], indexing="ij"))
+    assert Z[fast.ravel()].mean() < Z[slow.ravel()].mean()  # the fast one is the shallower
+    assert w.dt == pytest.approx(0.5 * 0.5 * w.h / vp.max(), rel=1e-14)
+    vs0, vp0 = _velocities(w, "trial")
+    assert np.all(vs0 == 200.0) and np.allclose(vp0, 400.0)
