@@ -925,7 +925,7 @@ def run_large_iteration(args):
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - t
     held = _bytes_in_use(torch, dev) - base
-    J0 = float(J)
+    J0 = float(J.detach())
     mt_inv = 1.0 / torch.tensor(ctx.mass_tilde(), device=dev)
     gl, gm = lam.grad.double(), mu.grad.double()
     ml, mm = lam.detach().double(), mu.detach().double()

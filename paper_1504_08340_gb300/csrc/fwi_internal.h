@@ -95,12 +95,11 @@ __device__ __forceinline__ bool node_ok(const Geo &g, int site, long long node) 
   return guard(g.oob, site, node, (long long)g.px * g.n[1] * g.n[2]) && guard(g.oob, site, node % g.px, g.n[0]);
 }
 
-// One RK4 stage is five kernels writing disjoint node sets; they read the same
+// One RK4 stage is four kernels writing disjoint node sets; they read the same
 // input and may run concurrently on different streams. Each launcher returns the
 // number of kernels it launched:
 //  launch_interior: nodes all of whose elements are interior (fwi_interior.cu);
-//  launch_pml:      nodes all of whose elements are PML, off the outer faces (fwi_pml.cu;
-//                   two kernels: the stress rows, then the displacement rows);
+//  launch_pml:      nodes all of whose elements are PML, off the outer faces (fwi_pml.cu);
 //  launch_shell:    the interface shell (fwi_stage.cu) and the PML nodes on the
 //                   outer faces of the grid (launch_pml_face, fwi_pml.cu).
 int launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s);
