@@ -146,6 +146,48 @@ def measured_traffic(workload_name, batch=1, nmat=0):
     return (one - mat) / shots * batch + mat
 
 
+TRAFFIC_COMMAND = ('ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none '
+                   '-k regex:"interior_kernel|shell_kernel|pml_kernel|pml_face_kernel" -s 16 -c 16 --csv '
+                   '--log-file traffic_layered.csv python bench.py --profile-forward 3 --max-batch 1')
+
+
+def traffic_summary(csv_path, workload_name):
+    """The per-stage DRAM traffic summary of the stage kernels from an ncu CSV log of
+    TRAFFIC_COMMAND (16 launches: the four kernels of each of the four stages of one
+    forward step of one shot), keyed to the current stage-kernel sources."""
+    import csv
+
+    per = {}
+    launches = set()
+    with open(csv_path) as f:
+        rows = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(rows):
+        name = r["Kernel Name"]
+        if name.endswith(")"):  # drop the argument list (template arguments may hold parentheses)
+            depth, i = 0, len(name) - 1
+            while i >= 0:
+                depth += {")": 1, "(": -1}.get(name[i], 0)
+                if depth == 0:
+                    break
+                i -= 1
+            name = name[:i]
+        if name.startswith("void "):
+            name = name[5:]
+        launches.add(r["ID"])
+        per.setdefault(name, {})
+        per[name][r["Metric Name"]] = per[name].get(r["Metric Name"], 0.0) + float(r["Metric Value"].replace(",", ""))
+    stages = len(launches) / 4
+    rd = sum(k.get("dram__bytes_read.sum", 0.0) for k in per.values()) / stages
+    wr = sum(k.get("dram__bytes_write.sum", 0.0) for k in per.values()) / stages
+    for k in per.values():  # durations in seconds
+        if "gpu__time_duration.sum" in k:
+            k["gpu__time_duration.sum"] *= 1e-9
+    return {"workload": workload_name, "shots_per_launch": 1, "csrc_sha256": kernel_sources_sha256(),
+            "stages_captured": stages, "kernel_launches_captured": len(launches),
+            "dram_bytes_per_stage": rd + wr, "dram_read_bytes_per_stage": rd, "dram_write_bytes_per_stage": wr,
+            "per_kernel": per, "command": TRAFFIC_COMMAND}
+
+
 WORKLOADS = {"layered_96x96x48": fi.layered_96x96x48, "grf_64x64x32": fi.grf_64x64x32}
 
 
@@ -1015,7 +1057,16 @@ def main():
                          "160x160x80 + 12 PML workload (4000 steps) over --large-shots shots")
     ap.add_argument("--large-shots", type=int, default=1)
     ap.add_argument("--large-backtracks", type=int, default=6)
+    ap.add_argument("--traffic-json", metavar="CSV",
+                    help="write profiles/stage_traffic_layered_96x96x48.json from an ncu CSV log of the "
+                         "stage-traffic capture (see TRAFFIC_COMMAND) and exit")
     args = ap.parse_args()
+    if args.traffic_json:
+        rec = traffic_summary(args.traffic_json, "layered_96x96x48")
+        with open(os.path.join(ROOT, "profiles", "stage_traffic_layered_96x96x48.json"), "w") as f:
+            json.dump(rec, f, indent=1)
+        print(json.dumps({k: v for k, v in rec.items() if k != "per_kernel"}))
+        return
     if args.full_evaluation:
         if "--warmup" not in sys.argv:
             args.warmup = 0
