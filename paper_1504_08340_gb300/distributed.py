@@ -5,10 +5,14 @@ gradient are sums over the shots (Sec. 3), so the path shards by shot: each rank
 evaluates a contiguous range of shots on its own GPU and the per-rank misfits and
 FP64 gradients are summed once per evaluation. That sum is the only exchange.
 
-The sum is formed in a fixed rank order (all-gather, then rank 0 + rank 1 + ...), so
-every rank holds the same bits whatever reduction tree the backend would use. The
-collectives run on the default process group (or the one passed in) with tensors on
-the gradients' device: an NCCL group for CUDA tensors, a gloo group for CPU ones.
+The sum is formed in a fixed rank order, rank 0 + rank 1 + ..., so every rank holds the
+same bits whatever reduction tree the backend would use. It runs as a chunked
+reduce-scatter and all-gather: the flattened (J, g_lambda, g_mu) is cut into one chunk per
+rank, an all-to-all hands rank r every rank's chunk r, rank r adds them in rank order,
+and an all-gather returns the summed chunks to every rank. Each rank holds about three
+copies of the gradient, whatever the number of ranks. The collectives run on the default
+process group (or the one passed in) with tensors on the gradients' device: an NCCL group
+for CUDA tensors, a gloo group for CPU ones.
 """
 from __future__ import annotations
 
@@ -43,13 +47,22 @@ def reduce_gradient(J: float, g_lambda, g_mu, group=None):
     n = g_lambda.numel()
     if g_mu.numel() != n or g_lambda.dtype != torch.float64 or g_mu.dtype != torch.float64:
         raise ValueError("g_lambda and g_mu must be FP64 tensors of one size")
-    flat = torch.cat([torch.tensor([J], dtype=torch.float64, device=g_lambda.device), g_lambda.reshape(-1),
-                      g_mu.reshape(-1)])
-    parts = [torch.empty_like(flat) for _ in range(_world(group))]
-    dist.all_gather(parts, flat, group=group)
-    total = parts[0].clone()
-    for p in parts[1:]:
-        total += p
+    world = _world(group)
+    length = 1 + 2 * n
+    chunk = -(-length // world)
+    send = torch.zeros(world * chunk, dtype=torch.float64, device=g_lambda.device)
+    send[0] = J
+    send[1:1 + n] = g_lambda.reshape(-1)
+    send[1 + n:length] = g_mu.reshape(-1)
+    recv = torch.empty_like(send)
+    dist.all_to_all_single(recv, send, group=group)  # recv[r chunk] = rank r's chunk of this rank
+    rows = recv.view(world, chunk)
+    mine = rows[0].clone()
+    for r in range(1, world):
+        mine += rows[r]
+    parts = [torch.empty(chunk, dtype=torch.float64, device=g_lambda.device) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    total = torch.cat(parts)[:length]
     return float(total[0]), total[1:1 + n].view(g_lambda.shape), total[1 + n:].view(g_mu.shape)
 
 

@@ -45,7 +45,7 @@ def _rank_main(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_reduce_gradient_is_the_rank_order_sum(tmp_path, world):
     import torch.multiprocessing as mp
 
