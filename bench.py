@@ -800,10 +800,13 @@ def run_precond_study(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     # ---- evaluation on held-out media
-    hist = {"plain": [], "learned": []}
+    # plain L-BFGS, L-BFGS with the lambda-direction biasing (25) (W = 1 at the first
+    # iteration, lowered linearly to 0 by the 50th, as Sec. 3.3.3 schedules it), and the
+    # network's updates with a backtracking line search
+    hist = {"plain": [], "biased": [], "learned": []}
     for k in range(args.study_test):
         lt, mt = truth(5000 + k)
-        for method in ("plain", "learned"):
+        for method in ("plain", "biased", "learned"):
             ctx.set_material(l0, m0)
             ctx.step_reset()
             J = ctx.misfit(obs)
@@ -813,6 +816,8 @@ def run_precond_study(args):
             for it in range(args.study_iters):
                 if method == "plain":
                     J = ctx.step(obs, first_step=0.05).J_new
+                elif method == "biased":
+                    J = ctx.step(obs, first_step=0.05, bias_w=max(0.0, 1.0 - it / 50.0)).J_new
                 else:
                     J, gl, gm = ctx.adjoint_gradient(obs)
                     lam, mu = (torch.tensor(a, device=dev) for a in ctx.get_material())
