@@ -364,7 +364,9 @@ fwi_status zero_state(fwi_ctx *c) {
 }
 
 // One RK4 step (4 fused stage kernels) of the forward (adj = false) or the
-// reversed-time adjoint (adj = true) system, with the point loads of the step.
+// reversed-time adjoint (adj = true) system, with the point loads of the step (source
+// samples, or receiver residuals). Both run the forward stage kernels (see below); the
+// transposed kernels serve fwi_rhs's adjoint rate.
 // nb shots (shot0 .. shot0 + nb - 1 for the sources) advance together; shot b's history
 // level goes to hist_slot + b * hstride
 fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot0, int nb, float *hist_slot, int64_t hstride) {
@@ -387,7 +389,12 @@ fwi_status rk4_step(fwi_ctx *c, bool adj, int n, int shot0, int nb, float *hist_
     a.nshot = nb;
     a.sstride = (int64_t)set_floats(c);
     a.hstride = hstride;
-    TRY(stage(c, adj, a));
+    // The adjoint sweep advances (w, W = tau(T)) rather than (w, T): tau is linear,
+    // node-local and constant in time, so applied to the transposed system's stress rows it
+    // gives exactly the forward system's form (tau on P(H) in the S rows, the plain stress
+    // columns in the u rows), and the forward stage kernels advance it. The displacement w,
+    // all the gradient reads, is the same; the stress slots hold tau(T).
+    TRY(stage(c, false, a));
     fwi::PointArgs p{};
     p.nnode_pad = (int64_t)c->geo.px * c->geo.n[1] * c->geo.n[2];
     p.oob = c->geo.oob;

@@ -101,6 +101,59 @@ def test_rhs_parity(oracle_mod, mesh, adjoint):
     _check_by_class(o, out, ref)
 
 
+def _tau(S, lam, mu):
+    """tau(S) = mu (S + diag S) + lam tr(S) I of symmetric tensors S[..., 6] (xx yy zz yz
+    xz xy, off-diagonals as stored), with per-node lam, mu."""
+    tr = S[..., 0] + S[..., 1] + S[..., 2]
+    out = np.empty_like(S)
+    for c in range(3):
+        out[..., c] = 2.0 * mu * S[..., c] + lam * tr
+    for c in range(3, 6):
+        out[..., c] = mu * S[..., c]
+    return out
+
+
+def _node_material(o, w, lam, mu, top):
+    """lambda, mu at every oracle node (natural order), the PML's taken from the nearest
+    interface node of the material grid (index clamp)."""
+    n = np.arange(o.nnode)
+    i, j, k = n % o.nn[0], (n // o.nn[0]) % o.nn[1], n // (o.nn[0] * o.nn[1])
+    lo = (w.npml, w.npml, w.npml if top else 0)
+    m = lam.shape  # (k, j, i)
+    kk = np.clip(k - 2 * lo[2], 0, m[0] - 1)
+    jj = np.clip(j - 2 * lo[1], 0, m[1] - 1)
+    ii = np.clip(i - 2 * lo[0], 0, m[2] - 1)
+    return lam.astype(np.float64)[kk, jj, ii], mu.astype(np.float64)[kk, jj, ii]
+
+
+@pytest.mark.parametrize("mesh", MESHES, ids=lambda m: f"{m['nx']}x{m['ny']}x{m['nz']}+{m['npml']}{'t' if m['top'] else ''}")
+def test_adjoint_sweep_runs_the_forward_form_on_tau_of_T(oracle_mod, mesh):
+    """The adjoint sweep advances (w, W = tau(T)) with the forward stage kernels: tau is
+    linear and node-local, so applying it to the transposed system's stress rows gives the
+    forward system's form (tau moves from the u rows' line points to the S rows). On a
+    random state (w, T): the forward-form rate of (w, tau(T)) has the transposed rate's u
+    rows and tau of its S rows, node by node."""
+    w = fi.tiny(nx=mesh["nx"], ny=mesh["ny"], nz=mesh["nz"], npml=mesh["npml"])
+    lam, mu = _random_medium(w, 6)
+    o = _oracle_for(oracle_mod, w, lam, mu, top_pml=mesh["top"])
+    pml, dirn = o.masks()
+    Y = fi.random_state(o.nnode, pml, dirn, seed=17, scale=1.0)
+    Y[:, :, 3:] *= 1e8
+    Y = _as_f64_of_f32(Y)
+    ln, mn = _node_material(o, w, lam, mu, mesh["top"])
+    YW = Y.copy()
+    for l in range(3):
+        YW[l, :, 3:] = _tau(Y[l, :, 3:], ln, mn)
+    with _ctx(w, top_pml=mesh["top"]) as ctx:
+        ctx.set_material(lam, mu)
+        r_adj = from_gpu_layout(ctx.rhs(to_gpu_layout(Y, ctx), adjoint=True), ctx)
+        r_fwd = from_gpu_layout(ctx.rhs(to_gpu_layout(_as_f64_of_f32(YW), ctx), adjoint=False), ctx)
+    ref = r_adj.copy()
+    for l in range(3):
+        ref[l, :, 3:] = _tau(r_adj[l, :, 3:], ln, mn)
+    _check_by_class(o, r_fwd, ref)
+
+
 def _check_by_class(o, out, ref, tol=2e-5):
     """Relative L2 per level, field group (u, S) and node set (interior, shell, outer-face
     PML, deep PML), so that an error confined to a small node set is not diluted by the
