@@ -196,7 +196,7 @@ def workload(name="grf_64x64x32"):
 
 
 def stage_bytes_per_step_17(ctx):
-    """The same stage traffic in the streaming model of the survey: 17 state accesses per
+    """The same stage traffic in a streaming model of 17 state accesses per
     variable per step (an RK4 accumulator read and written at every stage)."""
     p = ctx.npml_nodes
     n = ctx.nnode
