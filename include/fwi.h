@@ -302,8 +302,11 @@ fwi_status fwi_rhs(fwi_ctx *ctx, int adjoint, const float *state, float *rate, i
 /* The RK4 state at the end of the most recent sweep, in the layout of fwi_rhs
  * (27 fields of dims[5] floats, host or device): after fwi_forward(ctx, s, 1, ...)
  * it is shot s's state x(t_N) of (6) (displacement, rate and history levels, the
- * PML stresses). A diagnostic accessor, e.g. for energy checks; after a gradient
- * evaluation it holds the adjoint state instead. Caller-owned output; synchronous.
+ * PML stresses). A diagnostic accessor, e.g. for energy checks. After a gradient
+ * evaluation it holds the reversed-time adjoint state at its end instead, with
+ * tau(T) = mu (T + diag T) + lambda tr(T) I of the adjoint stress T in the stress slots
+ * (the adjoint sweep advances (w, tau(T)), which has the forward system's form).
+ * Caller-owned output; synchronous.
  * Errors: FWI_E_INVAL (null), FWI_E_STATE (no state buffers), FWI_E_CUDA. */
 fwi_status fwi_get_state(fwi_ctx *ctx, float *state, int on_device);
 
