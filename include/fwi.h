@@ -296,7 +296,10 @@ fwi_status fwi_get_mass_tilde(fwi_ctx *ctx, double *mtilde);
  * node (i, j, k) sits at offset (k * NJ + j) * PX + i of a field (PX = dims[8];
  * the padding entries i >= NI must be zero).
  * Displacement fields must be zero on the Dirichlet faces and history / stress
- * fields zero off the PML nodes. Errors: FWI_E_STATE (no material). */
+ * fields zero off the PML nodes. Device buffers (on_device = 1) must start on a
+ * 16-byte boundary (the stage kernels read the state with 16-byte and tensor copies).
+ * Errors: FWI_E_INVAL (null or unaligned), FWI_E_STATE (no material), FWI_E_TIMEOUT,
+ * FWI_E_CUDA. */
 fwi_status fwi_rhs(fwi_ctx *ctx, int adjoint, const float *state, float *rate, int on_device);
 
 /* The RK4 state at the end of the most recent sweep, in the layout of fwi_rhs
@@ -325,6 +328,17 @@ fwi_status fwi_get_state(fwi_ctx *ctx, float *state, int on_device);
  * The adjoint sweep always uses the specialised kernels. Not in the paper.
  * Errors: FWI_E_INVAL, FWI_E_NOMEM, FWI_E_CUDA. */
 fwi_status fwi_set_persistent(fwi_ctx *ctx, int enable, double wait_ms, int test_extra_arrivals);
+
+/* Bounded waits of the interior stage kernel: each plane of the stage input reaches the
+ * kernel's shared-memory ring as one tensor copy (TMA) that completes on an mbarrier, and
+ * every wait for one gives up after wait_ms milliseconds (0 < wait_ms <= 60000; 1000 when
+ * the context is created). A wait that gives up makes its thread block wait (again
+ * bounded) for its copies in flight and return; the call that ran the sweep returns
+ * FWI_E_TIMEOUT and the context stays usable. test_extra_bytes > 0 (at most 65536) makes
+ * every plane barrier expect that many bytes more than its copy delivers, so that the
+ * timeout path can be exercised; use 0 otherwise. Drops recorded graphs. Not in the
+ * paper. Errors: FWI_E_INVAL, FWI_E_CUDA. */
+fwi_status fwi_set_copy_wait(fwi_ctx *ctx, double wait_ms, int test_extra_bytes);
 
 /* CUDA graphs for the time loops: with enable = 1, each sweep of a later call (a forward
  * sweep, the adjoint sweep over the stored history, one checkpoint segment) is recorded by

@@ -325,7 +325,8 @@ fwi_status check_status(fwi_ctx *c) {
   if (st != 0) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    return fail(c, FWI_E_TIMEOUT, "a grid barrier of the persistent sweep gave up waiting");
+    return fail(c, FWI_E_TIMEOUT, "a bounded device wait gave up (a grid barrier of the persistent sweep, or a "
+                                  "plane copy of the interior kernel)");
   }
   return FWI_OK;
 }
@@ -336,8 +337,9 @@ fwi_status stage(fwi_ctx *c, bool adj, const fwi::StageArgs &a) {
   // fork: interior and interface/face kernels on the side streams, bulk PML here
   CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->stream));
   for (int i = 0; i < 2; i++) CUDA_TRY(c, cudaStreamWaitEvent(c->side[i], c->ev_fork, 0));
-  const int nk = fwi::launch_interior(c->geo, a, c->side[0]) + fwi::launch_shell(c->geo, a, adj, c->side[1]) +
-                 fwi::launch_pml(c->geo, a, adj, c->stream);
+  const int ni = fwi::launch_interior(c->geo, a, c->side[0]);
+  if (ni < 0) return fail(c, FWI_E_CUDA, "no tensor map for the stage input (not 16-byte aligned, or no driver entry)");
+  const int nk = ni + fwi::launch_shell(c->geo, a, adj, c->side[1]) + fwi::launch_pml(c->geo, a, adj, c->stream);
   for (int i = 0; i < 2; i++) {
     CUDA_TRY(c, cudaEventRecord(c->ev_join[i], c->side[i]));
     CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_join[i], 0));
@@ -817,6 +819,12 @@ fwi_status fwi_create(const fwi_config *cfg, fwi_ctx **out) {
     st = fail(c, FWI_E_CUDA, "error word clear failed");
 #endif
   g.oob = c->d_oob;
+  if (st == FWI_OK) st = dalloc(c, &c->d_status, 1);
+  if (st == FWI_OK && cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess)
+    st = fail(c, FWI_E_CUDA, "status word clear failed");
+  g.status = c->d_status;
+  g.wait_cycles = (long long)(1000.0 * 1e-3 * 2.2e9);  // about a second
+  g.copy_extra = 0;
   if (st == FWI_OK) {
     g.lam = c->d_lam;
     g.mu = c->d_mu;
@@ -1499,6 +1507,8 @@ fwi_status fwi_rhs(fwi_ctx *c, int adjoint, const float *state, float *rate, int
   TRY(check_stream(c));
   if (!c->have_material) return fail(c, FWI_E_STATE, "material not set");
   if (!state || !rate) return fail(c, FWI_E_INVAL, "null argument");
+  if (on_device && ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(rate)) & 15) != 0)
+    return fail(c, FWI_E_INVAL, "device state and rate must be 16-byte aligned");
   if (!c->state[0]) return fail(c, FWI_E_STATE, "no RK4 state buffers (a shot batch allocation failed)");
   const size_t n = (size_t)fwi::kFields * c->geo.stride;
   const float *in = state;
@@ -1751,6 +1761,19 @@ fwi_status fwi_set_persistent(fwi_ctx *c, int enable, double wait_ms, int test_e
     c->bar_extra = test_extra_arrivals;
   }
   c->persistent = enable != 0;
+  return FWI_OK;
+}
+
+fwi_status fwi_set_copy_wait(fwi_ctx *c, double wait_ms, int test_extra_bytes) {
+  if (!c) return FWI_E_INVAL;
+  TRY(check_stream(c));
+  if (!(wait_ms > 0.0 && wait_ms <= 60000.0)) return fail(c, FWI_E_INVAL, "wait_ms outside (0, 60000]");
+  if (test_extra_bytes < 0 || test_extra_bytes > 65536)
+    return fail(c, FWI_E_INVAL, "test_extra_bytes outside [0, 65536]");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->geo.wait_cycles = (long long)(wait_ms * 1e-3 * 2.2e9);
+  c->geo.copy_extra = test_extra_bytes;
+  drop_graphs(c);  // recorded sweeps hold the wait limits they were recorded with
   return FWI_OK;
 }
 

@@ -15,13 +15,19 @@
 // GB300 mapping: a block owns a 64 x 8 node tile in (x, y) and marches along
 // z through a chunk of planes. u (3 components) of planes K-2 .. K+2 sits in a
 // shared-memory ring (6 planes x 3 fields x 12 rows x 72 floats, 62.2 KB; rows
-// start at a 16-byte aligned x and are copied in 16-byte chunks); plane K+3
-// streams in with cp.async while plane K is computed. lambda and mu are read from
-// global memory (L1/L2 resident). Each thread computes a pair of nodes (even x,
-// odd x) of plane K.
+// start at a 16-byte aligned x). Each plane arrives as one tensor copy (TMA,
+// cp.async.bulk.tensor: a 72 x 12 x 1 x 3 box of the stage input, zero outside the
+// grid) issued by one thread and signalled on the ring slot's mbarrier; plane K+3
+// streams in while plane K is computed, and the block waits only for plane K+2
+// before it computes K. Every wait is bounded (Geo::wait_cycles). lambda and mu are
+// read from global memory (L1/L2 resident). Each thread computes a pair of nodes
+// (even x, odd x) of plane K.
 // Side types are template parameters, so every stencil access is a shared
 // load at a compile-time offset from one of five plane base registers.
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cstring>
 
 #include "fwi_internal.h"
 
@@ -34,21 +40,23 @@ constexpr int kTP = 32;             // node pairs per tile row (64 nodes)
 #endif
 constexpr int kTY = FWI_INT_TY;     // rows per tile
 // smem row: the tile's 64 nodes with a halo of 2 on each side, from a 16-byte aligned
-// start (at most 2 nodes before the halo), copied in 16-byte chunks
+// start (at most 2 nodes before the halo); it is also the tensor copy's box width
 constexpr int kTXS = 2 * kTP + 8;   // smem row pitch
-constexpr int kCPR = kTXS / 4;      // 16-byte chunks per row
 constexpr int kTYS = kTY + 4;
 constexpr int kFS = kTXS * kTYS;    // floats per field and plane
 constexpr int kNF = 3;              // u_x, u_y, u_z
 constexpr int kPS = kNF * kFS;      // floats per plane
 constexpr int kRing = 6;            // planes K-2 .. K+2 in use, K+3 in flight
-constexpr int kSmem = kRing * kPS * (int)sizeof(float);
+constexpr int kPlaneBytes = kPS * (int)sizeof(float);   // one tensor copy (10,368 bytes)
+constexpr int kSmem = kRing * kPlaneBytes + kRing * 8;  // the ring, then one mbarrier per slot
+static_assert(kPlaneBytes % 128 == 0, "tensor copies land on 128-byte aligned ring slots");
+static_assert(kTXS <= 256 && kTYS <= 256, "TMA box extents");
 
 enum { kC = 0, kL = 1, kR = 2 };
 // side set of a node along an axis: odd coordinate {C}, even {L, R}, top face {R}
 enum { kOdd = 0, kEven = 1, kTop = 2 };
 
-extern __shared__ float s_ring[];  // the plane ring (dynamic shared memory)
+extern __shared__ __align__(1024) float s_ring[];  // the plane ring, then the slot barriers
 
 struct Tile {
   int pl[5];  // ring offsets (floats) of the planes dz = -2..2
@@ -226,62 +234,102 @@ __device__ __forceinline__ void finish_node(const Geo &g, const StageArgs &a, in
   }
 }
 
-// asynchronous 16-byte global -> shared copy; src_bytes = 0 writes zeros
-__device__ __forceinline__ void cp_async16(float *dst, const float *src, int src_bytes) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+// ---- plane copies: mbarrier and TMA (PTX)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_init(uint64_t *b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// issue the copies of plane K (u of the stage input) of the tile into dst: rows
-// y0-2 .. y0+kTY+1, x from xs = (x0 - 2) rounded down to a multiple of 4. Chunks
-// outside the grid (rows, planes, x < 0 or x >= px) are zero-filled; the row padding
-// x in [NI, px) holds zeros in every state buffer.
-__device__ __forceinline__ void load_plane(const Geo &g, const StageArgs &a, float *dst, int K, int xs, int y0) {
-  const int64_t S = g.stride;
-  const bool kin = K >= 0 && K < g.n[2];
-  for (int idx = threadIdx.y * kTP + threadIdx.x; idx < kNF * kTYS * kCPR; idx += kTP * kTY) {
-    const int f = idx / (kTYS * kCPR), r = (idx / kCPR) % kTYS, ch = idx % kCPR;
-    const int gx = xs + 4 * ch, gy = y0 - 2 + r;
-    const bool ok = kin && gx >= 0 && gx < g.px && gy >= 0 && gy < g.n[1];
-    const float *src = ok ? a.Y + (int64_t)(9 + f) * S + ((int64_t)K * g.n[1] + gy) * g.px + gx : a.Y;
-    cp_async16(dst + f * kFS + r * kTXS + 4 * ch, src, ok ? 16 : 0);
-  }
+// the one arrival of a slot's phase, with the bytes its copy will deliver
+__device__ __forceinline__ void bar_arm(uint64_t *b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_done(uint64_t *b, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// wait for the phase of parity `parity` to complete; false after `limit` clock cycles
+__device__ __forceinline__ bool bar_wait(uint64_t *b, unsigned parity, long long limit) {
+  if (bar_done(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!bar_done(b, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+// box (x .. x+71, y .. y+11, plane z, fields f .. f+2) of the tensor map into dst
+__device__ __forceinline__ void copy_plane(float *dst, const CUtensorMap *tm, int x, int y, int z, int f, uint64_t *b) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(smem_u32(b))
+      : "memory");
 }
 
 #ifndef FWI_INT_MINB
 #define FWI_INT_MINB 2
 #endif
-__global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g, StageArgs a0) {
+// tm: the u fields of the stage input of the batch (see plane_map); the copies of a plane
+// are numbered from k0 - 2: copy q lands in ring slot q % kRing, and is that slot's
+// (q / kRing)-th phase
+__global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB)
+    interior_kernel(const __grid_constant__ CUtensorMap tm, Geo g, StageArgs a0) {
   float *smem = s_ring;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s_ring + kRing * kPS);
   const int kc = g.int_kc;                                   // planes per block
   const int nzc = (g.box_hi[2] - g.box_lo[2] + kc) / kc;     // z chunks per shot
-  const StageArgs a = shot_args(a0, blockIdx.z / nzc);
+  const int shot = blockIdx.z / nzc;
+  const StageArgs a = shot_args(a0, shot);
   const int bz = blockIdx.z % nzc;
   const int x0 = g.box_lo[0] - 1 + 2 * kTP * blockIdx.x;  // even: pairs (even, odd)
-  const int xs = (x0 - 2) & ~3;                            // first x of the smem rows
+  const int xs = (x0 - 2) & ~3;                            // first x of the smem rows (16-byte aligned)
   const int sh = x0 - 2 - xs;                              // 0 or 2
   const int y0 = g.box_lo[1] + kTY * blockIdx.y;
   const int k0 = g.box_lo[2] + kc * bz;
   const int k1 = min(k0 + kc - 1, g.box_hi[2]);
+  const int q0 = k0 - 2;                                   // plane of copy 0
+  const int f0 = kFields * shot + 9;                       // the shot's u_x field in the map
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+  const unsigned bytes = kPlaneBytes + (unsigned)g.copy_extra;
+  auto issue = [&](int K) {
+    uint64_t *b = &bar[(K - q0) % kRing];
+    bar_arm(b, bytes);
+    copy_plane(smem + ((K - q0) % kRing) * kPS, &tm, xs, y0 - 2, K, f0, b);
+  };
+  auto landed = [&](int K) { return bar_wait(&bar[(K - q0) % kRing], ((K - q0) / kRing) & 1, g.wait_cycles); };
+  // after a wait of this call gave up, later launches do nothing until the host has read
+  // it (one thread reads the word, so the whole block takes the same branch)
+  if (__syncthreads_or(lead && *(volatile int *)g.status != 0)) return;
+  if (lead) {
+    for (int s = 0; s < kRing; s++) bar_init(&bar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int K = k0 - 2; K <= k0 + 2; K++) issue(K);
+  }
+  __syncthreads();
   const int IE = x0 + 2 * threadIdx.x, IO = IE + 1, J = y0 + threadIdx.y;
   const bool rowok = J <= g.box_hi[1];
   const bool even_ok = rowok && IE >= g.box_lo[0] && IE <= g.box_hi[0];
   const bool odd_ok = rowok && IO >= g.box_lo[0] && IO <= g.box_hi[0];
   const int sy = (J & 1) ? kOdd : kEven;
   const float sc = -(g.inv_h * g.inv_h * (1.f / 3.f)) / g.rho;
-  for (int K = k0 - 2; K <= k0 + 2; K++) load_plane(g, a, smem + ((K + 12) % kRing) * kPS, K, xs, y0);
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncthreads();
-  for (int K = k0; K <= k1; K++) {
-    // plane K+3 streams into the free ring slot while plane K is computed
-    if (K + 1 <= k1) load_plane(g, a, smem + ((K + 3 + 12) % kRing) * kPS, K + 3, xs, y0);
-    cp_async_commit();
+  int K = k0;
+  bool ok = true;
+  for (; K <= k1; K++) {
+    // plane K+3 goes to the slot of plane K-3, which every thread finished with before the
+    // barrier that ended the previous plane
+    if (lead && K + 1 <= k1) issue(K + 3);
+    bool got = true;
+    if (K == k0)
+      for (int q = k0 - 2; q <= k0 + 1 && got; q++) got = landed(q);
+    got = got && landed(K + 2);
+    if (!got) atomicExch(g.status, 6);  // FWI_E_TIMEOUT
     Tile t;
 #pragma unroll
-    for (int d = 0; d < 5; d++) t.pl[d] = ((K + d - 2 + 12) % kRing) * kPS;
+    for (int d = 0; d < 5; d++) t.pl[d] = ((K + d - 2 - q0) % kRing) * kPS;
     const int sz = (K & 1) ? kOdd : ((K == 0 && !g.top_dir) ? kTop : kEven);
     t.o = (threadIdx.y + 2) * kTXS + 2 + sh + 2 * threadIdx.x;
     t.lam = g.lam;
@@ -290,8 +338,8 @@ __global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g,
     t.ms2 = g.m[0] * g.m[1];
     t.mi = ((K - 2 * g.lo[2]) * g.m[1] + (J - 2 * g.lo[1])) * g.m[0] + (IE - 2 * g.lo[0]);
     const int64_t rowbase = ((int64_t)K * g.n[1] + J) * g.px;
-    const bool e_ok = even_ok && node_ok(g, kSiteInterior, rowbase + IE);
-    const bool o_ok = odd_ok && node_ok(g, kSiteInterior, rowbase + IO);
+    const bool e_ok = got && even_ok && node_ok(g, kSiteInterior, rowbase + IE);
+    const bool o_ok = got && odd_ok && node_ok(g, kSiteInterior, rowbase + IO);
     Own oe, oo;
     if (e_ok) load_own(g, a, rowbase + IE, oe);
     if (o_ok) load_own(g, a, rowbase + IO, oo);
@@ -307,9 +355,51 @@ __global__ void __launch_bounds__(kTP *kTY, FWI_INT_MINB) interior_kernel(Geo g,
       node_accel_dispatch<kOdd>(t, sy, sz, sc, acc);
       finish_node(g, a, IO, J, K, t, oo, acc);
     }
-    cp_async_wait_all();
-    __syncthreads();
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      break;
+    }
   }
+  if (!ok && lead) {
+    // a wait gave up: before the block's shared memory is released, wait (bounded) for the
+    // copies it may still have in flight, the last kRing issued
+    const int last = max(k0 + 2, min(K + 3, k1 + 2));
+    for (int q = max(q0, last - kRing + 1); q <= last; q++) landed(q);
+  }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static const EncodeTiled fn = []() -> EncodeTiled {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// tensor map of the stage input Y of nshot shots as a 4-D FP32 tensor: x (the row pitch px),
+// y (NJ rows), z (NK planes), f (27 nshot fields, `stride` floats apart; shot b's field c is
+// 27 b + c, as the shots' state sets are 27 stride floats apart). Boxes are 72 x 12 x 1 x 3;
+// elements outside the tensor read as zero (the row padding x >= NI holds zeros in every
+// state buffer, so a box reads zero wherever the node grid ends).
+bool plane_map(const Geo &g, const StageArgs &a, CUtensorMap *tm) {
+  const EncodeTiled enc = encode_tiled();
+  if (!enc || ((uintptr_t)a.Y & 15) != 0 || (a.nshot > 1 && a.sstride != (int64_t)kFields * g.stride)) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.px, (cuuint64_t)g.n[1], (cuuint64_t)g.n[2],
+                              (cuuint64_t)kFields * (cuuint64_t)a.nshot};
+  const cuuint64_t pitch[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.px * g.n[1] * 4, (cuuint64_t)g.stride * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)kTXS, (cuuint32_t)kTYS, 1, (cuuint32_t)kNF};
+  const cuuint32_t step[4] = {1, 1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(a.Y), dims, pitch, box, step,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -323,7 +413,10 @@ int launch_interior(const Geo &g, const StageArgs &a, cudaStream_t s) {
   const int nx = g.box_hi[0] - (g.box_lo[0] - 1) + 1;
   const dim3 grd((nx + 2 * kTP - 1) / (2 * kTP), (g.box_hi[1] - g.box_lo[1] + kTY) / kTY,
                  (g.box_hi[2] - g.box_lo[2] + g.int_kc) / g.int_kc * a.nshot);
-  interior_kernel<<<grd, dim3(kTP, kTY), kSmem, s>>>(g, a);
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  if (!plane_map(g, a, &tm)) return -1;
+  interior_kernel<<<grd, dim3(kTP, kTY), kSmem, s>>>(tm, g, a);
   return 1;
 }
 

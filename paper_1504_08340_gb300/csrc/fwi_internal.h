@@ -55,6 +55,13 @@ struct Geo {
   const int *face;        // node numbers of the PML nodes on the grid's outer faces
   int nface;
   unsigned long long *oob;  // error word of the bounds-checked build (else null)
+  // bounded waits of interior_kernel on its plane copies: after wait_cycles clock cycles a
+  // wait gives up, sets *status to FWI_E_TIMEOUT (6) and the block returns; copy_extra > 0
+  // makes every plane barrier expect that many bytes more than the copy delivers (tests of
+  // the timeout path only)
+  int *status;
+  long long wait_cycles;
+  int copy_extra;
   // launch shapes (fwi_tune_tiles; they change no node's arithmetic)
   int int_kc;             // planes per block of interior_kernel
   int pml_seg;            // node pairs per x segment of a pml_kernel warp task (<= 32)
@@ -98,7 +105,9 @@ __device__ __forceinline__ bool node_ok(const Geo &g, int site, long long node) 
 // One RK4 stage is four kernels writing disjoint node sets; they read the same
 // input and may run concurrently on different streams. Each launcher returns the
 // number of kernels it launched:
-//  launch_interior: nodes all of whose elements are interior (fwi_interior.cu);
+//  launch_interior: nodes all of whose elements are interior (fwi_interior.cu); -1 if
+//                   the tensor map of the stage input could not be encoded (Y not
+//                   16-byte aligned, or the driver entry point missing);
 //  launch_pml:      nodes all of whose elements are PML, off the outer faces (fwi_pml.cu);
 //  launch_shell:    the interface shell (fwi_stage.cu) and the PML nodes on the
 //                   outer faces of the grid (launch_pml_face, fwi_pml.cu).

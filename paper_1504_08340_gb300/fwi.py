@@ -50,7 +50,8 @@ class StepInfo(C.Structure):
 # every symbol the header declares; the CPU test checks the library exports them all
 EXPORTS = ("fwi_create", "fwi_destroy", "fwi_last_error", "fwi_status_string", "fwi_bounds_checked", "fwi_get_dims",
            "fwi_set_material", "fwi_set_sources", "fwi_set_receivers", "fwi_forward", "fwi_misfit",
-           "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_get_state", "fwi_set_graphs", "fwi_set_persistent", "fwi_set_timing",
+           "fwi_adjoint_gradient", "fwi_get_mass_tilde", "fwi_rhs", "fwi_get_state", "fwi_set_graphs", "fwi_set_persistent", "fwi_set_copy_wait",
+           "fwi_set_timing",
            "fwi_get_timing", "fwi_reset_timing", "fwi_trace_misfit_noalloc", "fwi_step",
            "fwi_step_reset", "fwi_get_material", "fwi_set_checkpointing", "fwi_regularization",
            "fwi_set_shot_batch", "fwi_tune_shot_batch", "fwi_tune_tiles",
@@ -97,6 +98,7 @@ def load_library(path: str = None):
     lib.fwi_get_state.argtypes = [P, P, I]
     lib.fwi_set_graphs.argtypes = [P, I]
     lib.fwi_set_persistent.argtypes = [P, I, C.c_double, I]
+    lib.fwi_set_copy_wait.argtypes = [P, C.c_double, I]
     lib.fwi_set_timing.argtypes = [P, I]
     lib.fwi_get_timing.argtypes = [P, I, D, I64]
     lib.fwi_reset_timing.argtypes = [P]
@@ -362,6 +364,10 @@ class Context:
     def set_persistent(self, enable=True, wait_ms=1000.0, test_extra_arrivals=0):
         """Forward sweeps as one cooperative launch with bounded grid barriers (fwi_set_persistent)."""
         self._check(self.lib.fwi_set_persistent(self.ptr, int(enable), float(wait_ms), int(test_extra_arrivals)))
+
+    def set_copy_wait(self, wait_ms=1000.0, test_extra_bytes=0):
+        """Limit of the interior kernel's bounded waits on its plane copies (fwi_set_copy_wait)."""
+        self._check(self.lib.fwi_set_copy_wait(self.ptr, float(wait_ms), int(test_extra_bytes)))
 
     def set_graphs(self, enable=True):
         """Record each sweep once as a CUDA graph and replay it (fwi_set_graphs)."""

@@ -91,6 +91,7 @@ def test_null_context_is_rejected_without_touching_the_gpu():
         "fwi_get_state": (nul, nul, 0),
         "fwi_set_graphs": (nul, 1),
         "fwi_set_persistent": (nul, 1, ctypes.c_double(100.0), 0),
+        "fwi_set_copy_wait": (nul, ctypes.c_double(100.0), 0),
         "fwi_set_timing": (nul, 1),
         "fwi_get_timing": (nul, 0, nul, nul),
         "fwi_reset_timing": (nul,),
