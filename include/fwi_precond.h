@@ -40,7 +40,13 @@ extern "C" {
 /* y[co] = act(b[co] + sum_ci sum_t w[co][ci][t] x[ci][p + t - 1]) for every voxel p,
  * out-of-grid taps reading zero; act is ReLU when relu != 0, else the identity.
  * x: BF16 [cin][D][H][W]; w: BF16 [cout][cin][27]; b: FP32 [cout] or null (zero);
- * y: BF16 [cout][D][H][W], rounded to nearest even from the FP32 sum. */
+ * y: BF16 [cout][D][H][W], rounded to nearest even from the FP32 sum.
+ * Runs on the tensor cores (tcgen05 MMAs, BF16 operands, FP32 accumulation in tensor
+ * memory) as an implicit GEMM over 128-voxel tiles; the weights are first packed into
+ * 27 * ceil(cin/8) * 8 * ceil(cout/16) * 16 BF16 values (rounded up to whole chunks) of
+ * scratch that the call allocates and frees in stream order (cudaMallocAsync). A wait
+ * inside the kernel that gives up (not expected in operation) writes NaN to the outputs
+ * of its tile. FWI_E_CUDA also when the scratch cannot be allocated. */
 fwi_status fwi_nn_conv3d_forward(const uint16_t *x, const uint16_t *w, const float *b, int cin, int cout, int D,
                                  int H, int W, int relu, uint16_t *y, void *stream);
 

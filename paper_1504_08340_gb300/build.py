@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libfwi.so")
 SOURCES = ["fwi_api.cu", "fwi_kernels.cu", "fwi_stage.cu", "fwi_interior.cu", "fwi_pml.cu", "fwi_opt.cu", "fwi_noalloc.cu",
-           "fwi_precond.cu"]
+           "fwi_precond.cu", "fwi_conv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

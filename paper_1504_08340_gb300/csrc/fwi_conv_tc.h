@@ -1,0 +1,20 @@
+// fwi_conv_tc.h -- the tensor-core (tcgen05) convolutions of the learned
+// preconditioner (fwi_conv_tc.cu), called by fwi_nn_conv3d_forward and
+// fwi_nn_conv3d_backward_data. Not public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwi_tc {
+// y[co][p] = act(b[co] + sum_ci sum_t w[co][ci][t] x[ci][p + off(t)]) with the layouts of
+// fwi_nn_conv3d_forward; enqueues a weight pack into stream-ordered scratch, the
+// convolution and the scratch's release on s. Returns the first CUDA error.
+cudaError_t conv3d_forward_tc(const uint16_t *x, const uint16_t *w, const float *b, int cin, int cout, int D, int H,
+                              int W, int relu, uint16_t *y, cudaStream_t s);
+// dx[ci][p] = sum_co sum_t w[co][ci][t] dy[co][p - off(t)] with the layouts of
+// fwi_nn_conv3d_backward_data: the FP32 dy enters as three BF16 parts (hi, lo, lo2) per
+// channel, so the tensor-core products keep FP32 accuracy.
+cudaError_t conv3d_backward_data_tc(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
+                                    float *dx, cudaStream_t s);
+}  // namespace fwi_tc

@@ -2,24 +2,23 @@
 // convolutions forward and backward, ReLU backward, mean squared error and Adam, with
 // BF16 storage of activations and weights and FP32 accumulation (fwi_precond.h).
 //
-// The convolutions are direct: a thread owns one voxel and a block of 8 output (or,
-// backward, input) channels, walks the input channels and the 27 taps, and reads each
-// input value once per tap for its 8 channels. All threads of a warp read the same
-// weight, which L1 broadcasts. Every sum runs in a fixed order (channels, then taps;
-// weight gradients over fixed voxel chunks, then the chunks in order), so results
-// repeat bit for bit.
+// The forward and backward-data convolutions run on the tensor cores as implicit GEMMs
+// (fwi_conv_tc.cu). The weight gradient is direct: a block owns a voxel chunk of one
+// (output, input) channel pair and walks the 27 taps. Every sum runs in a fixed order
+// (the tensor-core sums in the fixed order of their MMAs; weight gradients over fixed voxel
+// chunks, then the chunks in order), so results repeat bit for bit.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cmath>
 
+#include "fwi_conv_tc.h"
 #include "fwi_precond.h"
 
 namespace {
 
 constexpr int kT = 256;                 // threads per block
-constexpr int kCB = 8;                  // channels per thread in the convolutions
 constexpr int kChunk = kT * 16;         // voxels per partial sum of the weight gradient
 constexpr int kTaps = 27;
 constexpr int64_t kMaxVox = int64_t(1) << 34;
@@ -27,93 +26,6 @@ constexpr int kRedBlocks = 1024;
 
 __device__ __forceinline__ float bf2f(uint16_t u) { return __uint_as_float((unsigned)u << 16); }
 __device__ __forceinline__ uint16_t f2bf(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
-
-__global__ void __launch_bounds__(kT) conv_fwd_kernel(const uint16_t *__restrict__ x, const uint16_t *__restrict__ w,
-                                                      const float *__restrict__ b, int cin, int cout, int D, int H,
-                                                      int W, int relu, uint16_t *__restrict__ y) {
-  const int64_t nv = (int64_t)D * H * W;
-  const int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x;
-  if (p >= nv) return;
-  const int co0 = blockIdx.y * kCB;
-  const int nco = min(kCB, cout - co0);
-  const int px = (int)(p % W);
-  const int64_t r = p / W;
-  const int py = (int)(r % H), pz = (int)(r / H);
-  float acc[kCB];
-#pragma unroll
-  for (int c = 0; c < kCB; c++) acc[c] = (c < nco && b) ? b[co0 + c] : 0.f;
-  const int64_t wstride = (int64_t)cin * kTaps;  // between output channels
-  for (int ci = 0; ci < cin; ci++) {
-    const uint16_t *xc = x + (int64_t)ci * nv;
-    const uint16_t *wc = w + ((int64_t)co0 * cin + ci) * kTaps;
-    for (int kz = 0; kz < 3; kz++) {
-      const int z = pz + kz - 1;
-      if (z < 0 || z >= D) continue;
-      for (int ky = 0; ky < 3; ky++) {
-        const int yy = py + ky - 1;
-        if (yy < 0 || yy >= H) continue;
-        const uint16_t *row = xc + ((int64_t)z * H + yy) * W;
-        for (int kx = 0; kx < 3; kx++) {
-          const int xx = px + kx - 1;
-          if (xx < 0 || xx >= W) continue;
-          const float xv = bf2f(row[xx]);
-          const int t = (kz * 3 + ky) * 3 + kx;
-#pragma unroll
-          for (int c = 0; c < kCB; c++)
-            if (c < nco) acc[c] = fmaf(bf2f(wc[c * wstride + t]), xv, acc[c]);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < kCB; c++)
-    if (c < nco) {
-      const float v = relu ? fmaxf(acc[c], 0.f) : acc[c];
-      y[(int64_t)(co0 + c) * nv + p] = f2bf(v);
-    }
-}
-
-// x at p feeds y at p + 1 - k along each axis (tap k), so dx[p] gathers dy there
-__global__ void __launch_bounds__(kT) conv_bwd_data_kernel(const float *__restrict__ dy,
-                                                           const uint16_t *__restrict__ w, int cin, int cout, int D,
-                                                           int H, int W, float *__restrict__ dx) {
-  const int64_t nv = (int64_t)D * H * W;
-  const int64_t p = (int64_t)blockIdx.x * kT + threadIdx.x;
-  if (p >= nv) return;
-  const int ci0 = blockIdx.y * kCB;
-  const int nci = min(kCB, cin - ci0);
-  const int px = (int)(p % W);
-  const int64_t r = p / W;
-  const int py = (int)(r % H), pz = (int)(r / H);
-  float acc[kCB];
-#pragma unroll
-  for (int c = 0; c < kCB; c++) acc[c] = 0.f;
-  for (int co = 0; co < cout; co++) {
-    const float *dyc = dy + (int64_t)co * nv;
-    const uint16_t *wc = w + ((int64_t)co * cin + ci0) * kTaps;
-    for (int kz = 0; kz < 3; kz++) {
-      const int z = pz + 1 - kz;
-      if (z < 0 || z >= D) continue;
-      for (int ky = 0; ky < 3; ky++) {
-        const int yy = py + 1 - ky;
-        if (yy < 0 || yy >= H) continue;
-        const float *row = dyc + ((int64_t)z * H + yy) * W;
-        for (int kx = 0; kx < 3; kx++) {
-          const int xx = px + 1 - kx;
-          if (xx < 0 || xx >= W) continue;
-          const float dv = row[xx];
-          const int t = (kz * 3 + ky) * 3 + kx;
-#pragma unroll
-          for (int c = 0; c < kCB; c++)
-            if (c < nci) acc[c] = fmaf(bf2f(wc[c * kTaps + t]), dv, acc[c]);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < kCB; c++)
-    if (c < nci) dx[(int64_t)(ci0 + c) * nv + p] = acc[c];
-}
 
 // partial sums over voxel chunk blockIdx.x of dy[co] x[ci](p + t - 1) (27 taps) and of
 // dy[co] (slot 27), for co = blockIdx.y, ci = blockIdx.z
@@ -335,19 +247,17 @@ extern "C" {
 fwi_status fwi_nn_conv3d_forward(const uint16_t *x, const uint16_t *w, const float *b, int cin, int cout, int D,
                                  int H, int W, int relu, uint16_t *y, void *stream) {
   if (!x || !w || !y || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
-  const int64_t nv = (int64_t)D * H * W;
-  const dim3 grid((unsigned)((nv + kT - 1) / kT), (unsigned)((cout + kCB - 1) / kCB));
-  conv_fwd_kernel<<<grid, kT, 0, (cudaStream_t)stream>>>(x, w, b, cin, cout, D, H, W, relu, y);
-  return launched();
+  return fwi_tc::conv3d_forward_tc(x, w, b, cin, cout, D, H, W, relu, y, (cudaStream_t)stream) == cudaSuccess
+             ? FWI_OK
+             : FWI_E_CUDA;
 }
 
 fwi_status fwi_nn_conv3d_backward_data(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
                                        float *dx, void *stream) {
   if (!dy || !w || !dx || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
-  const int64_t nv = (int64_t)D * H * W;
-  const dim3 grid((unsigned)((nv + kT - 1) / kT), (unsigned)((cin + kCB - 1) / kCB));
-  conv_bwd_data_kernel<<<grid, kT, 0, (cudaStream_t)stream>>>(dy, w, cin, cout, D, H, W, dx);
-  return launched();
+  return fwi_tc::conv3d_backward_data_tc(dy, w, cin, cout, D, H, W, dx, (cudaStream_t)stream) == cudaSuccess
+             ? FWI_OK
+             : FWI_E_CUDA;
 }
 
 int64_t fwi_nn_conv3d_backward_weight_work(int cin, int cout, int D, int H, int W) {

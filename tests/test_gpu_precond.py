@@ -4,7 +4,8 @@
 Tolerances follow the arithmetic: a forward output is the FP32 sum rounded to BF16,
 so it is within 2^-8 of the exact value relative to its size (half a BF16 step plus
 the FP32 sum's error); the FP32 backward sums of at most a few thousand products
-agree with FP64 to 1e-5 relative; bitwise where nothing is rounded differently
+agree with FP64 to 1e-5 relative (the tensor-core backward-data sums to the bound of
+_bwd_data_tol); bitwise where nothing is rounded differently
 (ReLU masks, BF16 conversions, the BF16 copy Adam writes)."""
 import ctypes as C
 
@@ -72,6 +73,36 @@ def test_conv_forward(cin, cout, relu):
     assert np.mean(_bits(y) == P.bf16_bits(ref)) > 0.99
 
 
+@pytest.mark.parametrize("cin,cout,shape", [(37, 300, (7, 13, 17)), (32, 112, (6, 16, 16)), (112, 16, (3, 5, 9))])
+def test_conv_forward_tensor_core_tiles(cin, cout, shape):
+    # the tensor-core tiling at its edges: two output-channel tiles (256 + 44), input
+    # channels off the 8-channel core width (K = 27 x 40, ragged against 64-wide chunks),
+    # voxel counts off the 128-voxel tile, and wide K (27 x 112)
+    rng = np.random.default_rng(cin + cout)
+    xd, xv = _bf16(rng.standard_normal((cin, *shape)))
+    wd, wv = _bf16(rng.standard_normal((cout, cin, 27)) / np.sqrt(27 * cin))
+    b = rng.standard_normal(cout).astype(np.float32)
+    y = torch.empty((cout, *shape), dtype=torch.bfloat16, device="cuda")
+    assert _lib().fwi_nn_conv3d_forward(_p(xd), _p(wd), _p(_f32(b)), cin, cout, *shape, 1, _p(y), _s()) == 0
+    ref = np.maximum(P.conv3d(xv, wv, b.astype(np.float64)), 0)
+    got = _vals(y)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5)
+    assert np.mean(_bits(y) == P.bf16_bits(ref)) > 0.99
+    # the same call again gives the same bits
+    y2 = torch.empty_like(y)
+    assert _lib().fwi_nn_conv3d_forward(_p(xd), _p(wd), _p(_f32(b)), cin, cout, *shape, 1, _p(y2), _s()) == 0
+    assert torch.equal(y.view(torch.int16), y2.view(torch.int16))
+
+
+def _bwd_data_tol(cout):
+    """Relative L2 bound of the backward-data sums: K = 27 x 3 x ceil(cout / 8) x 8 exact
+    products (three BF16 parts of each FP32 gradient value, BF16 weights) accumulated in
+    FP32 on the tensor cores, whose adds align and round within each 16-product MMA: about
+    2^-23 sqrt(K) relative."""
+    k = 27 * 3 * ((cout + 7) // 8 * 8)
+    return 2.0 ** -23 * np.sqrt(k)
+
+
 @pytest.mark.parametrize("cin,cout", [(3, 10), (9, 2)])
 def test_conv_backward_data(cin, cout):
     rng = np.random.default_rng(7 + cin)
@@ -81,8 +112,26 @@ def test_conv_backward_data(cin, cout):
     dyd = _f32(dy)
     assert _lib().fwi_nn_conv3d_backward_data(_p(dyd), _p(wd), cin, cout, *SHAPE, _p(dx), _s()) == 0
     ref = P.conv3d_backward_data(dy.astype(np.float64), wv, cin)
-    assert rel_l2(dx.cpu().numpy(), ref) < 1e-6
+    assert rel_l2(dx.cpu().numpy(), ref) < _bwd_data_tol(cout)
     assert np.abs(dx.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("cin,cout,shape", [(300, 37, (3, 5, 9)), (32, 112, (6, 16, 16))])
+def test_conv_backward_data_tensor_core_tiles(cin, cout, shape):
+    # two output tiles of the GEMM (256 + 44 input channels), gradient channels off the
+    # 8-channel core width (three BF16 parts each), voxel counts off the 128-voxel tile;
+    # FP32 accuracy from the split gradient, and the same bits on a second call
+    rng = np.random.default_rng(cin * 3 + cout)
+    dy = (rng.standard_normal((cout, *shape)) * np.exp(rng.uniform(-8, 8, (cout, *shape)))).astype(np.float32)
+    wd, wv = _bf16(rng.standard_normal((cout, cin, 27)))
+    dx = torch.empty((cin, *shape), dtype=torch.float32, device="cuda")
+    dyd = _f32(dy)
+    assert _lib().fwi_nn_conv3d_backward_data(_p(dyd), _p(wd), cin, cout, *shape, _p(dx), _s()) == 0
+    ref = P.conv3d_backward_data(dy.astype(np.float64), wv, cin)
+    assert rel_l2(dx.cpu().numpy(), ref) < _bwd_data_tol(cout)
+    dx2 = torch.empty_like(dx)
+    assert _lib().fwi_nn_conv3d_backward_data(_p(dyd), _p(wd), cin, cout, *shape, _p(dx2), _s()) == 0
+    assert torch.equal(dx, dx2)
 
 
 @pytest.mark.parametrize("cin,cout,shape", [(3, 5, SHAPE), (2, 3, (20, 20, 24))])
