@@ -52,7 +52,9 @@ fwi_status fwi_nn_conv3d_forward(const uint16_t *x, const uint16_t *w, const flo
 
 /* The transposed convolution: dx[ci][p] = sum_co sum_t w[co][ci][t] dy[co][p - t + 1],
  * the gradient of sum(dy * y) with respect to x for the pre-activation y.
- * dy: FP32 [cout][D][H][W]; w: BF16 [cout][cin][27]; dx: FP32 [cin][D][H][W]. */
+ * dy: FP32 [cout][D][H][W]; w: BF16 [cout][cin][27]; dx: FP32 [cin][D][H][W].
+ * On the tensor cores as the forward call, with dy taken as three BF16 parts per value
+ * (hi, lo, lo2; their sum is dy to 2^-24), so the exact BF16 products keep FP32 accuracy. */
 fwi_status fwi_nn_conv3d_backward_data(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
                                        float *dx, void *stream);
 
@@ -60,8 +62,11 @@ fwi_status fwi_nn_conv3d_backward_data(const float *dy, const uint16_t *w, int c
 int64_t fwi_nn_conv3d_backward_weight_work(int cin, int cout, int D, int H, int W);
 
 /* dw[co][ci][t] = sum_p dy[co][p] x[ci][p + t - 1] and db[co] = sum_p dy[co][p]: the
- * gradients of sum(dy * y) with respect to the weights and biases. Partial sums over
- * fixed voxel chunks, then a sum of the chunks in order.
+ * gradients of sum(dy * y) with respect to the weights and biases. On the tensor cores:
+ * per slice of 2048 voxels one GEMM of the im2col matrix of x (with a row of ones for db)
+ * against dy taken as three BF16 parts per value (so the products keep FP32 accuracy),
+ * FP32 partial sums into `work`, then the slices added in order. Copies of x
+ * (channels-last) and of the split dy are allocated and freed in stream order.
  * dy: FP32 [cout][D][H][W]; x: BF16 [cin][D][H][W]; dw: FP32 [cout][cin][27];
  * db: FP32 [cout] or null; work: FP32 scratch (fwi_nn_conv3d_backward_weight_work). */
 fwi_status fwi_nn_conv3d_backward_weight(const float *dy, const uint16_t *x, int cin, int cout, int D, int H, int W,

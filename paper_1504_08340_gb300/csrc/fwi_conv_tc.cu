@@ -313,6 +313,243 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 
 namespace {
 
+// ---- weight gradient: dW[m][co] = sum_p A[p][m] dy[co][p], m = t Cp + ci (tap t, input
+// channel ci) and one more row m = 27 Cp of ones (the bias gradient), over a slice of
+// kSlice voxels per block; then the slices summed in order.
+//   - A is the im2col matrix of x in MN-major layout: a core matrix is 8 voxels (along K)
+//     of 16 bytes along M (8 channels of one tap), so a row is one 16-byte load from the
+//     channels-last copy; core (mg, kg) at mg * 1024 + kg * 128 (LBO = 128 along K, SBO =
+//     1024 along M);
+//   - B is the gradient in K-major layout, three BF16 parts per channel: a core row is 8
+//     consecutive voxels of one channel and part (16 bytes of the split copy), core (kg, ng)
+//     at kg * (N / 8) * 128 + ng * 128; each chunk runs 3 x 4 MMAs into one accumulator.
+constexpr int kSlice = 2048;          // voxels per block (K per block before the split)
+constexpr int kWgSbo = 1024;          // A: bytes between cores along M (8 cores along K)
+constexpr int kWgABytes = 16 * kWgSbo;  // 128 rows x 64 voxels
+
+// dys[s][co][p] = part s of dy[co][p] (as split_channels_last), zero for co >= cout or
+// p >= nv: rows of nvp = nv rounded up to kSlice voxels
+__global__ void split_channels_first(const float *__restrict__ dy, int64_t nv, int64_t nvp, int cout, int cop,
+                                     uint16_t *__restrict__ dys) {
+  const int64_t total = (int64_t)cop * nvp;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i % nvp;
+    const int co = (int)(i / nvp);
+    float r = (co < cout && p < nv) ? __ldg(dy + (int64_t)co * nv + p) : 0.f;
+#pragma unroll
+    for (int part = 0; part < 3; part++) {
+      const uint16_t h = __bfloat16_as_ushort(__float2bfloat16_rn(r));
+      dys[((int64_t)part * cop + co) * nvp + p] = h;
+      r -= __uint_as_float((uint32_t)h << 16);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    wgrad_kernel(const uint16_t *__restrict__ xcl, const uint16_t *__restrict__ dys, int cp, int cop, int nt_n,
+                 int tmem_cols, int mrows, int D, int H, int W, int64_t nvp, float *__restrict__ part) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int bpart = nt_n * kKC * 2;  // one part's B chunk
+  const int bbuf = 3 * bpart;
+  uint64_t *done = reinterpret_cast<uint64_t *>(sm + 2 * kWgABytes + 2 * bbuf);  // [2]
+  unsigned *tslot = reinterpret_cast<unsigned *>(done + 2);
+  int *abort_flag = reinterpret_cast<int *>(tslot + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t nv = (int64_t)D * H * W;
+  const int slice = blockIdx.x, mt = blockIdx.y, nt = blockIdx.z;
+  const int64_t v0 = (int64_t)slice * kSlice;
+  const unsigned lbo_b = (unsigned)(nt_n / 8) * 128u;
+  const int nchunk = kSlice / kKC;
+  if (tid == 0) {
+    bar_init(&done[0]);
+    bar_init(&done[1]);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tslot;
+  const uint32_t idesc = instr_desc(nt_n) | (1u << 15);  // A MN-major
+
+  int issued = 0;
+  bool ok = true;
+  for (int c = 0; c < nchunk; c++) {
+    const int s = c & 1;
+    unsigned char *sa = sm + s * kWgABytes;
+    unsigned char *sb = sm + 2 * kWgABytes + s * bbuf;
+    if (c >= 2 && !bar_wait(&done[s], ((c - 2) >> 1) & 1)) atomicExch(abort_flag, 1);
+    const int64_t pc = v0 + (int64_t)c * kKC;  // first voxel of the chunk
+    // A: 16 x 8 cores of 8 rows (voxels): 1024 rows, 4 per thread
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int r = tid + j * kThreads;  // row id: (mg, kg, row)
+      const int mg = r >> 6, kg = (r >> 3) & 7, rw = r & 7;
+      const int m0 = mt * 128 + mg * 8;
+      const int t = m0 / cp, ci0 = m0 % cp;
+      const int64_t p = pc + kg * 8 + rw;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (p < nv && m0 < mrows) {
+        if (t < 27) {
+          const int vx = (int)(p % W), vy = (int)(p / W % H), vz = (int)(p / W / H);
+          const int qx = vx + t % 3 - 1, qy = vy + t / 3 % 3 - 1, qz = vz + t / 9 - 1;
+          if (qx >= 0 && qx < W && qy >= 0 && qy < H && qz >= 0 && qz < D)
+            v = __ldg(reinterpret_cast<const uint4 *>(xcl + (((int64_t)qz * H + qy) * W + qx) * cp + ci0));
+        } else {
+          v.x = 0x3F80u;  // the ones row: BF16 1.0 in its first element
+        }
+      }
+      *reinterpret_cast<uint4 *>(sa + mg * kWgSbo + kg * 128 + rw * 16) = v;
+    }
+    // B: three parts of nt_n channels x 8 cores of 8 voxels
+    for (int r = tid; r < 3 * nt_n * 8; r += kThreads) {
+      const int part_i = r / (nt_n * 8), rr = r % (nt_n * 8);
+      const int n = rr >> 3, kg = rr & 7;
+      const int co = nt * nt_n + n;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (co < cop)
+        v = __ldg(reinterpret_cast<const uint4 *>(dys + ((int64_t)part_i * cop + co) * nvp + pc + kg * 8));
+      *reinterpret_cast<uint4 *>(sb + part_i * bpart + kg * lbo_b + (n >> 3) * 128 + (n & 7) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (*(volatile int *)abort_flag != 0) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int pi = 0; pi < 3; pi++)
+#pragma unroll
+        for (int ks = 0; ks < kKC / 16; ks++) {
+          const uint64_t da = smem_desc(su32(sa) + ks * 256, 128, kWgSbo);
+          const uint64_t db = smem_desc(su32(sb) + pi * bpart + 2 * ks * lbo_b, lbo_b, 128);
+          const unsigned acc = (c > 0 || pi > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       su32(&done[s]))
+                   : "memory");
+    }
+    issued = c + 1;  // every thread counts the chunks thread 0 committed
+  }
+  if (*(volatile int *)abort_flag != 0) ok = false;
+  if (issued > 0 && !bar_wait(&done[(issued - 1) & 1], ((issued - 1) >> 1) & 1)) ok = false;
+  ok = __syncthreads_and(ok) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // partial sums of this slice: part[slice][co][m], lanes = consecutive m
+  const int q = warp & 3, chalf = warp >> 2;
+  const int m = mt * 128 + q * 32 + lane;
+  const int cols_half = nt_n / 2;
+  const int mpad = gridDim.y * 128;
+  for (int c0 = chalf * cols_half; c0 < (chalf + 1) * cols_half; c0 += 8) {
+    uint32_t r[8];
+    const unsigned ta = tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int co = nt * nt_n + c0 + j;
+      part[((int64_t)slice * (gridDim.z * nt_n) + co) * mpad + m] = ok ? __uint_as_float(r[j]) : __uint_as_float(0x7FC00000u);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// dw[co][ci][t] and db[co]: the slices' partial sums added in slice order
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int nslice, int ncol, int mpad, int cin, int cout,
+                                    int cp, float *__restrict__ dw, float *__restrict__ db) {
+  const int64_t total = (int64_t)cout * (cin * 27 + 1);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int co = (int)(i / (cin * 27 + 1)), j = (int)(i % (cin * 27 + 1));
+    const bool bias = j == cin * 27;
+    const int ci = bias ? 0 : j / 27, t = bias ? 0 : j % 27;
+    const int m = bias ? 27 * cp : t * cp + ci;
+    float acc = 0.f;
+    for (int sl = 0; sl < nslice; sl++) acc += part[((int64_t)sl * ncol + co) * mpad + m];
+    if (bias) {
+      if (db) db[co] = acc;
+    } else {
+      dw[((int64_t)co * cin + ci) * 27 + t] = acc;
+    }
+  }
+}
+
+}  // namespace
+
+// floats of partial sums conv3d_backward_weight_tc needs
+int64_t conv3d_backward_weight_tc_work(int cin, int cout, int D, int H, int W) {
+  const int cp = (cin + 7) / 8 * 8;
+  const int64_t nv = (int64_t)D * H * W;
+  const int64_t nslice = (nv + kSlice - 1) / kSlice;
+  const int64_t mpad = ((int64_t)27 * cp + 1 + 127) / 128 * 128;
+  const int n16 = (cout + 15) / 16 * 16;
+  const int nt_n = n16 < kMaxN ? n16 : kMaxN;
+  const int64_t ncol = (int64_t)((cout + nt_n - 1) / nt_n) * nt_n;
+  return nslice * ncol * mpad;
+}
+
+cudaError_t conv3d_backward_weight_tc(const float *dy, const uint16_t *x, int cin, int cout, int D, int H, int W,
+                                      float *dw, float *db, float *work, cudaStream_t s) {
+  const int cp = (cin + 7) / 8 * 8;
+  const int cop = (cout + 7) / 8 * 8;
+  const int64_t nv = (int64_t)D * H * W;
+  const int64_t nslice = (nv + kSlice - 1) / kSlice;
+  const int64_t nvp = nslice * kSlice;
+  const int mrows = 27 * cp + 1;
+  const int mtiles = (mrows + 127) / 128;
+  const int n16 = (cout + 15) / 16 * 16;
+  const int nt_n = n16 < kMaxN ? n16 : kMaxN;
+  const int ntiles = (cout + nt_n - 1) / nt_n;
+  if (nslice > 0x7fffffff || mtiles > 65535 || ntiles > 65535) return cudaErrorInvalidValue;
+  int tmem_cols = 32;
+  while (tmem_cols < nt_n) tmem_cols *= 2;
+  const int max_blocks = 512 / tmem_cols;
+  int smem = 2 * kWgABytes + 2 * 3 * nt_n * kKC * 2 + 64;
+  const int floor_smem = kSmPerSM / (max_blocks + 1) - 1024 + 16;
+  if (smem < floor_smem) smem = floor_smem;
+  if (smem > 232448) return cudaErrorInvalidValue;  // more than a block's shared memory
+  cudaError_t e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  uint16_t *xcl = nullptr, *dys = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&xcl), (size_t)nv * cp * sizeof(uint16_t), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&dys), (size_t)3 * cop * nvp * sizeof(uint16_t), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(xcl, s);
+    return e;
+  }
+  const int64_t xb = (nv * (cp / 8) + 255) / 256, yb = ((int64_t)cop * nvp + 255) / 256;
+  to_channels_last<<<(unsigned)(xb < 65536 ? xb : 65536), 256, 0, s>>>(x, nv, cin, cp, xcl);
+  split_channels_first<<<(unsigned)(yb < 65536 ? yb : 65536), 256, 0, s>>>(dy, nv, nvp, cout, cop, dys);
+  wgrad_kernel<<<dim3((unsigned)nslice, (unsigned)mtiles, (unsigned)ntiles), kThreads, smem, s>>>(
+      xcl, dys, cp, cop, nt_n, tmem_cols, mrows, D, H, W, nvp, work);
+  const int64_t nout = (int64_t)cout * (cin * 27 + 1);
+  wgrad_reduce_kernel<<<(unsigned)((nout + 255) / 256 < 65536 ? (nout + 255) / 256 : 65536), 256, 0, s>>>(
+      work, (int)nslice, ntiles * nt_n, mtiles * 128, cin, cout, cp, dw, db);
+  e = cudaGetLastError();
+  const cudaError_t f1 = cudaFreeAsync(dys, s), f2 = cudaFreeAsync(xcl, s);
+  return e != cudaSuccess ? e : (f1 != cudaSuccess ? f1 : f2);
+}
+
+namespace {
+
 // the GEMM over n_out output rows (tiles of up to 256) with reduce channels cpa per tap;
 // src: the channels-last source the caller's `prepare` fills (nv x cpa BF16)
 template <bool BWD, class Prepare>

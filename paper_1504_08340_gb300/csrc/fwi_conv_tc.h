@@ -1,6 +1,6 @@
 // fwi_conv_tc.h -- the tensor-core (tcgen05) convolutions of the learned
-// preconditioner (fwi_conv_tc.cu), called by fwi_nn_conv3d_forward and
-// fwi_nn_conv3d_backward_data. Not public ABI.
+// preconditioner (fwi_conv_tc.cu), called by fwi_nn_conv3d_forward,
+// fwi_nn_conv3d_backward_data and fwi_nn_conv3d_backward_weight. Not public ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,4 +17,11 @@ cudaError_t conv3d_forward_tc(const uint16_t *x, const uint16_t *w, const float 
 // channel, so the tensor-core products keep FP32 accuracy.
 cudaError_t conv3d_backward_data_tc(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
                                     float *dx, cudaStream_t s);
+// dw[co][ci][t] = sum_p dy[co][p] x[ci][p + off(t)], db[co] = sum_p dy[co][p] with the
+// layouts of fwi_nn_conv3d_backward_weight: per 2048-voxel slice one GEMM (im2col of x
+// against the three BF16 parts of dy, plus a row of ones for db) into `work`, then the
+// slices added in order. conv3d_backward_weight_tc_work: the floats `work` must hold.
+int64_t conv3d_backward_weight_tc_work(int cin, int cout, int D, int H, int W);
+cudaError_t conv3d_backward_weight_tc(const float *dy, const uint16_t *x, int cin, int cout, int D, int H, int W,
+                                      float *dw, float *db, float *work, cudaStream_t s);
 }  // namespace fwi_tc

@@ -2,11 +2,10 @@
 // convolutions forward and backward, ReLU backward, mean squared error and Adam, with
 // BF16 storage of activations and weights and FP32 accumulation (fwi_precond.h).
 //
-// The forward and backward-data convolutions run on the tensor cores as implicit GEMMs
-// (fwi_conv_tc.cu). The weight gradient is direct: a block owns a voxel chunk of one
-// (output, input) channel pair and walks the 27 taps. Every sum runs in a fixed order
-// (the tensor-core sums in the fixed order of their MMAs; weight gradients over fixed voxel
-// chunks, then the chunks in order), so results repeat bit for bit.
+// The three convolutions (forward, backward data, weight gradient) run on the tensor
+// cores as implicit GEMMs (fwi_conv_tc.cu). Every sum runs in a fixed order (the MMAs in
+// a fixed sequence; weight gradients over fixed voxel slices, then the slices in order),
+// so results repeat bit for bit.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,83 +18,11 @@
 namespace {
 
 constexpr int kT = 256;                 // threads per block
-constexpr int kChunk = kT * 16;         // voxels per partial sum of the weight gradient
-constexpr int kTaps = 27;
 constexpr int64_t kMaxVox = int64_t(1) << 34;
 constexpr int kRedBlocks = 1024;
 
 __device__ __forceinline__ float bf2f(uint16_t u) { return __uint_as_float((unsigned)u << 16); }
 __device__ __forceinline__ uint16_t f2bf(float f) { return __bfloat16_as_ushort(__float2bfloat16_rn(f)); }
-
-// partial sums over voxel chunk blockIdx.x of dy[co] x[ci](p + t - 1) (27 taps) and of
-// dy[co] (slot 27), for co = blockIdx.y, ci = blockIdx.z
-__global__ void __launch_bounds__(kT) conv_bwd_w_partial_kernel(const float *__restrict__ dy,
-                                                                const uint16_t *__restrict__ x, int cin, int cout,
-                                                                int D, int H, int W, float *__restrict__ part) {
-  __shared__ float red[kT / 32][kTaps + 1];
-  const int64_t nv = (int64_t)D * H * W;
-  const int64_t chunk = blockIdx.x;
-  const int co = blockIdx.y, ci = blockIdx.z;
-  const float *dyc = dy + (int64_t)co * nv;
-  const uint16_t *xc = x + (int64_t)ci * nv;
-  float acc[kTaps + 1];
-#pragma unroll
-  for (int t = 0; t <= kTaps; t++) acc[t] = 0.f;
-  const int64_t p1 = min(nv, (chunk + 1) * (int64_t)kChunk);
-  for (int64_t p = chunk * kChunk + threadIdx.x; p < p1; p += kT) {
-    const int px = (int)(p % W);
-    const int64_t r = p / W;
-    const int py = (int)(r % H), pz = (int)(r / H);
-    const float dv = dyc[p];
-    acc[kTaps] += dv;
-#pragma unroll
-    for (int kz = 0; kz < 3; kz++) {
-      const int z = pz + kz - 1;
-      const bool vz = z >= 0 && z < D;
-#pragma unroll
-      for (int ky = 0; ky < 3; ky++) {
-        const int yy = py + ky - 1;
-        const bool vy = vz && yy >= 0 && yy < H;
-#pragma unroll
-        for (int kx = 0; kx < 3; kx++) {
-          const int xx = px + kx - 1;
-          const int t = (kz * 3 + ky) * 3 + kx;
-          if (vy && xx >= 0 && xx < W) acc[t] = fmaf(dv, bf2f(xc[((int64_t)z * H + yy) * W + xx]), acc[t]);
-        }
-      }
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int t = 0; t <= kTaps; t++) {
-    float s = acc[t];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) red[warp][t] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x <= kTaps) {
-    float s = 0.f;
-#pragma unroll
-    for (int q = 0; q < kT / 32; q++) s += red[q][threadIdx.x];
-    part[((chunk * cout + co) * (int64_t)cin + ci) * (kTaps + 1) + threadIdx.x] = s;
-  }
-}
-
-__global__ void __launch_bounds__(kT) conv_bwd_w_sum_kernel(const float *__restrict__ part, int64_t nchunk, int cin,
-                                                            int cout, float *__restrict__ dw, float *__restrict__ db) {
-  const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
-  const int64_t npair = (int64_t)cout * cin;
-  if (i >= npair * (kTaps + 1)) return;
-  const int v = (int)(i % (kTaps + 1));
-  const int64_t pair = i / (kTaps + 1);  // co * cin + ci
-  float s = 0.f;
-  for (int64_t c = 0; c < nchunk; c++) s += part[(c * npair + pair) * (kTaps + 1) + v];
-  if (v < kTaps)
-    dw[pair * kTaps + v] = s;
-  else if (db && pair % cin == 0)
-    db[pair / cin] = s;
-}
 
 __global__ void __launch_bounds__(kT) relu_bwd_kernel(const float *__restrict__ dy, const uint16_t *__restrict__ y,
                                                       int64_t n, float *__restrict__ out) {
@@ -262,21 +189,16 @@ fwi_status fwi_nn_conv3d_backward_data(const float *dy, const uint16_t *w, int c
 
 int64_t fwi_nn_conv3d_backward_weight_work(int cin, int cout, int D, int H, int W) {
   if (!sizes_ok(cin, cout, D, H, W)) return 0;
-  const int64_t nchunk = ((int64_t)D * H * W + kChunk - 1) / kChunk;
-  return nchunk * cout * (int64_t)cin * (kTaps + 1);
+  return fwi_tc::conv3d_backward_weight_tc_work(cin, cout, D, H, W);
 }
 
 fwi_status fwi_nn_conv3d_backward_weight(const float *dy, const uint16_t *x, int cin, int cout, int D, int H, int W,
                                          float *dw, float *db, float *work, void *stream) {
   if (!dy || !x || !dw || !work || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
-  const int64_t nchunk = ((int64_t)D * H * W + kChunk - 1) / kChunk;
-  if (nchunk > 0x7fffffff) return FWI_E_INVAL;
-  const cudaStream_t s = (cudaStream_t)stream;
-  conv_bwd_w_partial_kernel<<<dim3((unsigned)nchunk, (unsigned)cout, (unsigned)cin), kT, 0, s>>>(dy, x, cin, cout, D,
-                                                                                                 H, W, work);
-  const int64_t nout = (int64_t)cout * cin * (kTaps + 1);
-  conv_bwd_w_sum_kernel<<<(unsigned)((nout + kT - 1) / kT), kT, 0, s>>>(work, nchunk, cin, cout, dw, db);
-  return launched();
+  return fwi_tc::conv3d_backward_weight_tc(dy, x, cin, cout, D, H, W, dw, db, work, (cudaStream_t)stream) ==
+                 cudaSuccess
+             ? FWI_OK
+             : FWI_E_CUDA;
 }
 
 fwi_status fwi_nn_relu_backward(const float *dy, const uint16_t *y, int64_t n, float *out, void *stream) {

@@ -134,9 +134,11 @@ def test_conv_backward_data_tensor_core_tiles(cin, cout, shape):
     assert torch.equal(dx, dx2)
 
 
-@pytest.mark.parametrize("cin,cout,shape", [(3, 5, SHAPE), (2, 3, (20, 20, 24))])
+@pytest.mark.parametrize("cin,cout,shape", [(3, 5, SHAPE), (2, 3, (20, 20, 24)), (37, 300, (7, 20, 33))])
 def test_conv_backward_weight(cin, cout, shape):
-    """The second shape spans three voxel chunks of the partial sums, the last ragged."""
+    """The second shape spans five 2048-voxel slices of the partial sums, the last ragged;
+    the third nine tensor-core row tiles (27 x 40 tap-channel rows and the bias row), two
+    output-channel tiles (256 + 44) and three slices."""
     lib = _lib()
     rng = np.random.default_rng(17 + cin)
     dy = rng.standard_normal((cout, *shape)).astype(np.float32)
