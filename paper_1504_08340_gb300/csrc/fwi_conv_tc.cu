@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   int *abort_flag = reinterpret_cast<int *>(tslot + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nv = (int64_t)D * H * W;
-  const int slice = blockIdx.x, mt = blockIdx.y, nt = blockIdx.z;
+  // the row tiles of a slice are neighbours in the grid, so they read its voxels while L2
+  // still holds them
+  const int mt = blockIdx.x, slice = blockIdx.y, nt = blockIdx.z;
   const int64_t v0 = (int64_t)slice * kSlice;
   const unsigned lbo_b = (unsigned)(nt_n / 8) * 128u;
   const int nchunk = kSlice / kKC;
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   const int q = warp & 3, chalf = warp >> 2;
   const int m = mt * 128 + q * 32 + lane;
   const int cols_half = nt_n / 2;
-  const int mpad = gridDim.y * 128;
+  const int mpad = gridDim.x * 128;
   for (int c0 = chalf * cols_half; c0 < (chalf + 1) * cols_half; c0 += 8) {
     uint32_t r[8];
     const unsigned ta = tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0;
@@ -517,7 +519,7 @@ cudaError_t conv3d_backward_weight_tc(const float *dy, const uint16_t *x, int ci
   const int n16 = (cout + 15) / 16 * 16;
   const int nt_n = n16 < kMaxN ? n16 : kMaxN;
   const int ntiles = (cout + nt_n - 1) / nt_n;
-  if (nslice > 0x7fffffff || mtiles > 65535 || ntiles > 65535) return cudaErrorInvalidValue;
+  if (nslice > 65535 || ntiles > 65535) return cudaErrorInvalidValue;
   int tmem_cols = 32;
   while (tmem_cols < nt_n) tmem_cols *= 2;
   const int max_blocks = 512 / tmem_cols;
@@ -538,7 +540,7 @@ cudaError_t conv3d_backward_weight_tc(const float *dy, const uint16_t *x, int ci
   const int64_t xb = (nv * (cp / 8) + 255) / 256, yb = ((int64_t)cop * nvp + 255) / 256;
   to_channels_last<<<(unsigned)(xb < 65536 ? xb : 65536), 256, 0, s>>>(x, nv, cin, cp, xcl);
   split_channels_first<<<(unsigned)(yb < 65536 ? yb : 65536), 256, 0, s>>>(dy, nv, nvp, cout, cop, dys);
-  wgrad_kernel<<<dim3((unsigned)nslice, (unsigned)mtiles, (unsigned)ntiles), kThreads, smem, s>>>(
+  wgrad_kernel<<<dim3((unsigned)mtiles, (unsigned)nslice, (unsigned)ntiles), kThreads, smem, s>>>(
       xcl, dys, cp, cop, nt_n, tmem_cols, mrows, D, H, W, nvp, work);
   const int64_t nout = (int64_t)cout * (cin * 27 + 1);
   wgrad_reduce_kernel<<<(unsigned)((nout + 255) / 256 < 65536 ? (nout + 255) / 256 : 65536), 256, 0, s>>>(

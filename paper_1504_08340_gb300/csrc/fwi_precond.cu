@@ -167,6 +167,12 @@ unsigned grid_for(int64_t n) {
 
 fwi_status launched() { return cudaGetLastError() == cudaSuccess ? FWI_OK : FWI_E_CUDA; }
 
+// sizes the tensor-core tiling cannot take come back as cudaErrorInvalidValue, before any
+// device work
+fwi_status tc_status(cudaError_t e) {
+  return e == cudaSuccess ? FWI_OK : (e == cudaErrorInvalidValue ? FWI_E_INVAL : FWI_E_CUDA);
+}
+
 }  // namespace
 
 extern "C" {
@@ -174,17 +180,13 @@ extern "C" {
 fwi_status fwi_nn_conv3d_forward(const uint16_t *x, const uint16_t *w, const float *b, int cin, int cout, int D,
                                  int H, int W, int relu, uint16_t *y, void *stream) {
   if (!x || !w || !y || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
-  return fwi_tc::conv3d_forward_tc(x, w, b, cin, cout, D, H, W, relu, y, (cudaStream_t)stream) == cudaSuccess
-             ? FWI_OK
-             : FWI_E_CUDA;
+  return tc_status(fwi_tc::conv3d_forward_tc(x, w, b, cin, cout, D, H, W, relu, y, (cudaStream_t)stream));
 }
 
 fwi_status fwi_nn_conv3d_backward_data(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
                                        float *dx, void *stream) {
   if (!dy || !w || !dx || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
-  return fwi_tc::conv3d_backward_data_tc(dy, w, cin, cout, D, H, W, dx, (cudaStream_t)stream) == cudaSuccess
-             ? FWI_OK
-             : FWI_E_CUDA;
+  return tc_status(fwi_tc::conv3d_backward_data_tc(dy, w, cin, cout, D, H, W, dx, (cudaStream_t)stream));
 }
 
 int64_t fwi_nn_conv3d_backward_weight_work(int cin, int cout, int D, int H, int W) {
@@ -195,10 +197,7 @@ int64_t fwi_nn_conv3d_backward_weight_work(int cin, int cout, int D, int H, int 
 fwi_status fwi_nn_conv3d_backward_weight(const float *dy, const uint16_t *x, int cin, int cout, int D, int H, int W,
                                          float *dw, float *db, float *work, void *stream) {
   if (!dy || !x || !dw || !work || !sizes_ok(cin, cout, D, H, W)) return FWI_E_INVAL;
-  return fwi_tc::conv3d_backward_weight_tc(dy, x, cin, cout, D, H, W, dw, db, work, (cudaStream_t)stream) ==
-                 cudaSuccess
-             ? FWI_OK
-             : FWI_E_CUDA;
+  return tc_status(fwi_tc::conv3d_backward_weight_tc(dy, x, cin, cout, D, H, W, dw, db, work, (cudaStream_t)stream));
 }
 
 fwi_status fwi_nn_relu_backward(const float *dy, const uint16_t *y, int64_t n, float *out, void *stream) {
