@@ -42,19 +42,22 @@ extern "C" {
  * x: BF16 [cin][D][H][W]; w: BF16 [cout][cin][27]; b: FP32 [cout] or null (zero);
  * y: BF16 [cout][D][H][W], rounded to nearest even from the FP32 sum.
  * Runs on the tensor cores (tcgen05 MMAs, BF16 operands, FP32 accumulation in tensor
- * memory) as an implicit GEMM over 128-voxel tiles; the weights are first packed into
- * 27 * ceil(cin/8) * 8 * ceil(cout/16) * 16 BF16 values (rounded up to whole chunks) of
- * scratch that the call allocates and frees in stream order (cudaMallocAsync). A wait
- * inside the kernel that gives up (not expected in operation) writes NaN to the outputs
- * of its tile. FWI_E_CUDA also when the scratch cannot be allocated. */
+ * memory) as an implicit GEMM over tiles of 8 x 16 voxels of one plane: a TMA box brings
+ * the tile of x with its halo, and the 27 taps are shifted views of it. Two scratch copies
+ * are allocated and freed in stream order (cudaMallocAsync): x with its channels padded to
+ * a multiple of 32 (BF16, group-major) and the weights packed for the MMAs. A wait inside
+ * the kernel that gives up (not expected in operation) writes NaN to the outputs of its
+ * tile. FWI_E_INVAL for sizes the tiling cannot take (D > 65535); FWI_E_CUDA also when the
+ * scratch cannot be allocated. */
 fwi_status fwi_nn_conv3d_forward(const uint16_t *x, const uint16_t *w, const float *b, int cin, int cout, int D,
                                  int H, int W, int relu, uint16_t *y, void *stream);
 
 /* The transposed convolution: dx[ci][p] = sum_co sum_t w[co][ci][t] dy[co][p - t + 1],
  * the gradient of sum(dy * y) with respect to x for the pre-activation y.
  * dy: FP32 [cout][D][H][W]; w: BF16 [cout][cin][27]; dx: FP32 [cin][D][H][W].
- * On the tensor cores as the forward call, with dy taken as three BF16 parts per value
- * (hi, lo, lo2; their sum is dy to 2^-24), so the exact BF16 products keep FP32 accuracy. */
+ * On the tensor cores in the tile form of the forward call (taps mirrored), with dy taken
+ * as three BF16 parts per value (hi, lo, lo2; their sum is dy to 2^-24), so the exact BF16
+ * products keep FP32 accuracy; the sums run in FP32 on the tensor cores. */
 fwi_status fwi_nn_conv3d_backward_data(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
                                        float *dx, void *stream);
 

@@ -1,53 +1,42 @@
-// fwi_conv_tc.cu -- the forward 3x3x3 convolution of the learned preconditioner on the
-// fifth-generation tensor cores (tcgen05, sm_103a), as an implicit GEMM:
+// fwi_conv_tc.cu -- the 3x3x3 convolutions of the learned preconditioner on the
+// fifth-generation tensor cores (tcgen05, sm_103a), as implicit GEMMs with BF16 operands
+// in shared memory and FP32 accumulators in tensor memory (TMEM):
 //
-//   D[p][co] = sum_k A[p][k] B[co][k],  A[p][t Cp + ci] = x[ci][p + off(t)],
-//                                       B[co][t Cp + ci] = w[co][ci][t],
+//   forward         y[co][p]  = act(b[co] + sum_t sum_ci w[co][ci][t] x[ci][p + off(t)])
+//   backward data   dx[ci][p] = sum_t sum_co w[co][ci][t] dy[co][p - off(t)]
+//   weight gradient dw[co][ci][t] = sum_p dy[co][p] x[ci][p + off(t)], db[co] = sum_p dy[co][p]
 //
-// p a voxel, t one of the 27 taps (kz, ky, kx; kx fastest), ci an input channel (Cp =
-// cin rounded up to 8, the extra channels zero), out-of-grid taps reading zero. Products
-// of BF16 values are exact and the sums run in FP32 in tensor memory (TMEM).
+// t one of the 27 taps (kz, ky, kx; kx fastest), out-of-grid taps reading zero. Products
+// of BF16 values are exact; the FP32 gradients of the backward passes enter as three BF16
+// parts (hi, lo, lo2 with hi + lo + lo2 = dy to 2^-24), so their products stay exact too.
+// Operands use the no-swizzle canonical layouts: a core matrix is 8 rows of 16 bytes
+// stored contiguously; LBO is the byte stride between core matrices along K and SBO along
+// M (or N), in both K-major and MN-major operands. One thread issues the tcgen05.mma and
+// commits them to an mbarrier; the epilogue reads the accumulator with tcgen05.ld.
 //
-// A block (8 warps) owns 128 consecutive voxels (the GEMM's M) and a tile of up to 256
-// output channels (N, a multiple of 16). K runs in chunks of 64 (four MMAs of K = 16)
-// through two shared-memory buffers:
-//   - the weight chunk is a contiguous image (packed once per call by pack_kernel in
-//     the layout the MMA reads) and arrives by one bulk asynchronous copy that completes
-//     on the buffer's "loaded" mbarrier;
-//   - the im2col chunk is gathered by the threads from a channels-last copy of x
-//     (xcl[p][Cp], made once per call by to_channels_last): a thread owns a voxel and
-//     four core columns, each 8 channels of one tap, i.e. one 16-byte load and one
-//     16-byte store;
-//   - one thread issues the four tcgen05.mma and commits them to the buffer's "done"
-//     mbarrier, which the gather of chunk c + 2 waits for before it reuses the buffer.
-// Operands use the no-swizzle K-major canonical layout: a core matrix is 8 rows of 16
-// bytes (8 BF16 along K) stored contiguously; core (kg, mg) of a chunk sits at
-// kg * LBO + mg * 128 bytes. After the last commit the accumulator goes TMEM -> registers
-// (tcgen05.ld, a warp reads the 32 lanes = voxels of its quarter) -> bias, ReLU, BF16 ->
-// y[co][p], coalesced across the voxels.
+// The forward and backward-data passes use the tile form (tile_conv_kernel): a TMA box of
+// the input with its halo, and the 27 taps as shifted MMA views of it. The weight gradient
+// (wgrad_kernel) gathers im2col rows from a channels-last copy into an MN-major operand.
 //
-// Every mbarrier wait is bounded (about a second). A wait that gives up marks the block
-// failed: it waits (bounded) for the MMAs it issued, writes NaN to its outputs (so the
-// caller's loss turns non-finite) and frees its TMEM.
+// Every mbarrier wait is bounded (about a second). A block whose wait gives up waits
+// (bounded) for what it issued, writes NaN to its outputs (so the caller's loss turns
+// non-finite) and frees its TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cstring>
 
 #include "fwi_conv_tc.h"
 
 namespace fwi_tc {
 namespace {
 
-constexpr int kM = 128;          // voxels per block (MMA M)
-constexpr int kKC = 64;          // K per chunk: 8 core columns, 4 MMAs of K = 16
-constexpr int kThreads = 256;    // 8 warps
+constexpr int kM = 128;          // MMA M: voxels (forward, backward data) or tap-channel rows
+constexpr int kKC = 64;          // K per chunk of the weight gradient: 4 MMAs of K = 16
+constexpr int kThreads = 256;    // threads of a weight-gradient block
 constexpr int kMaxN = 256;       // output channels per block (MMA N <= 256)
-constexpr int kABytes = kM * kKC * 2;     // 16 KB im2col chunk
-constexpr int kBBytes = kMaxN * kKC * 2;  // <= 32 KB weight chunk
-constexpr int kLboA = (kM / 8) * 128;     // between core columns of the A chunk (2 KB)
-// shared memory: A[2], B[2] (2 x N x 128 bytes), then the barriers and the TMEM slots
-constexpr int kOffB = 2 * kABytes;
-constexpr int kSmemMax = kOffB + 2 * kBBytes + 64;
 constexpr int kSmPerSM = 233472;  // shared memory of an SM (228 KB); 1 KB more is reserved per block
 constexpr int kMinBlocks = 4;     // blocks per SM the register budget allows (64 registers)
 constexpr long long kWaitCycles = 2000000000LL;  // about a second
@@ -99,214 +88,6 @@ __global__ void to_channels_last(const uint16_t *__restrict__ x, int64_t nv, int
       if (c0 + e < cin) v[e >> 1] |= (uint32_t)__ldg(x + (int64_t)(c0 + e) * nv + p) << (16 * (e & 1));
     *reinterpret_cast<uint4 *>(xcl + p * cp + c0) = make_uint4(v[0], v[1], v[2], v[3]);
   }
-}
-
-// packed weights: for output-channel tile nt and chunk c, the Nt x 64 chunk image in the
-// layout above (core (kg, ng) at kg * (Nt / 8) * 128 + ng * 128, row n % 8, 8 k each).
-// Row n of B is an output channel of the GEMM (co forward, ci backward); column k = t cpa
-// + c' reads source channel c' of tap t, whose weight channel is c' % cgrp (the source of
-// the backward pass holds three BF16 parts of each gradient channel, cgrp apart).
-__global__ void pack_kernel(const uint16_t *__restrict__ w, int n_rows, int n_red, int cgrp, int cpa, bool bwd,
-                            int nt_n, int nchunk, int ntiles, uint16_t *__restrict__ out) {
-  const int64_t total = (int64_t)ntiles * nchunk * nt_n * kKC;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int kk = (int)(i % 8), row = (int)(i / 8 % 8);
-    const int64_t r = i / 64;
-    const int ng = (int)(r % (nt_n / 8)), kg = (int)(r / (nt_n / 8) % 8);
-    const int64_t tc = r / (nt_n / 8) / 8;  // tile * nchunk + chunk
-    const int c = (int)(tc % nchunk), nt = (int)(tc / nchunk);
-    const int n = nt * nt_n + ng * 8 + row;
-    const int64_t k = (int64_t)c * kKC + kg * 8 + kk;
-    const int t = (int)(k / cpa), cc = (int)(k % cpa) % cgrp;
-    uint16_t v = 0;
-    if (n < n_rows && cc < n_red && t < 27)
-      v = w[(bwd ? (int64_t)cc * n_rows + n : (int64_t)n * n_red + cc) * 27 + t];
-    out[i] = v;
-  }
-}
-
-// src[p][s cop + co] = part s of dy[co][p] (s = 0, 1, 2: hi, lo, lo2 with hi + lo + lo2 =
-// dy to within 2^-24 relative; each part the BF16 rounding of what the earlier parts left),
-// zero for cout <= co < cop: thread per voxel and 8 channels
-__global__ void split_channels_last(const float *__restrict__ dy, int64_t nv, int cout, int cop,
-                                    uint16_t *__restrict__ src) {
-  const int cpa = 3 * cop, groups = cpa / 8;
-  const int64_t total = nv * groups;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = i % nv;
-    const int g0 = (int)(i / nv) * 8;
-    const int part = g0 / cop, co0 = g0 % cop;
-    uint32_t v[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int e = 0; e < 8; e++) {
-      if (co0 + e >= cout) continue;
-      float r = __ldg(dy + (int64_t)(co0 + e) * nv + p);
-      uint16_t h = 0;
-      for (int q = 0; q <= part; q++) {
-        h = __bfloat16_as_ushort(__float2bfloat16_rn(r));
-        r -= __uint_as_float((uint32_t)h << 16);
-      }
-      v[e >> 1] |= (uint32_t)h << (16 * (e & 1));
-    }
-    *reinterpret_cast<uint4 *>(src + p * cpa + g0) = make_uint4(v[0], v[1], v[2], v[3]);
-  }
-}
-
-// BWD = false: y = BF16 [n_out][nv] of act(bias + D) with taps at p + off(t) (forward);
-// BWD = true: y = FP32 [n_out][nv] of D with taps at p - off(t) (backward data)
-template <bool BWD>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-    igemm_kernel(const uint16_t *__restrict__ xcl, const uint16_t *__restrict__ wpack, const float *__restrict__ bias,
-                 int cout, int cp, int nt_n, int tmem_cols, int nchunk, int D, int H, int W, int relu,
-                 void *__restrict__ yout) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  const int b_bytes = nt_n * kKC * 2;
-  uint64_t *loaded = reinterpret_cast<uint64_t *>(sm + kOffB + 2 * b_bytes);  // [2]
-  uint64_t *done = loaded + 2;                                      // [2]
-  unsigned *tslot = reinterpret_cast<unsigned *>(done + 2);  // TMEM address, then the committed count
-  int *abort_flag = reinterpret_cast<int *>(tslot + 2);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t nv = (int64_t)D * H * W;
-  const int64_t p0 = (int64_t)blockIdx.x * kM;
-  const int nt = blockIdx.y;
-  const unsigned lbo_b = (unsigned)(nt_n / 8) * 128u;
-  const uint16_t *wtile = wpack + (int64_t)nt * nchunk * nt_n * kKC;
-
-  // the thread's voxel (gather) and its half of each chunk's 8 core columns
-  const int m = tid & (kM - 1), half = tid >> 7;
-  const int64_t p = p0 + m;
-  const bool pin = p < nv;
-  const int vx = (int)(p % W), vy = (int)(p / W % H), vz = (int)(p / W / H);
-
-  if (tid == 0) {
-    for (int i = 0; i < 2; i++) {
-      bar_init(&loaded[i]);
-      bar_init(&done[i]);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                 "r"(tmem_cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const unsigned tmem = *tslot;
-  const uint32_t idesc = instr_desc(nt_n);
-
-  int issued = 0;        // chunks whose MMAs thread 0 committed
-  int copy_pending = -1;  // thread 0: the chunk whose weight copy it has not yet waited for
-  bool ok = true;
-  for (int c = 0; c < nchunk; c++) {
-    const int s = c & 1;
-    unsigned char *sa = sm + s * kABytes;
-    unsigned char *sb = sm + kOffB + s * b_bytes;
-    // the MMAs of chunk c - 2 read this buffer
-    if (c >= 2 && !bar_wait(&done[s], ((c - 2) >> 1) & 1)) atomicExch(abort_flag, 1);
-    if (tid == 0 && *(volatile int *)abort_flag == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&loaded[s])), "r"(b_bytes)
-                   : "memory");
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(sb)),
-          "l"(wtile + (int64_t)c * nt_n * kKC), "r"(b_bytes), "r"(su32(&loaded[s]))
-          : "memory");
-      copy_pending = c;
-    }
-    // im2col: core columns 4 half .. 4 half + 3 of the chunk, each 8 channels of one tap
-    uint4 v[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int k0 = c * kKC + (4 * half + j) * 8;
-      const int t = k0 / cp, ci0 = k0 % cp;
-      v[j] = make_uint4(0u, 0u, 0u, 0u);
-      if (pin && t < 27) {
-        constexpr int sg = BWD ? -1 : 1;
-        const int qx = vx + sg * (t % 3 - 1), qy = vy + sg * (t / 3 % 3 - 1), qz = vz + sg * (t / 9 - 1);
-        if (qx >= 0 && qx < W && qy >= 0 && qy < H && qz >= 0 && qz < D)
-          v[j] = __ldg(reinterpret_cast<const uint4 *>(xcl + (((int64_t)qz * H + qy) * W + qx) * cp + ci0));
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-      *reinterpret_cast<uint4 *>(sa + (4 * half + j) * kLboA + (m >> 3) * 128 + (m & 7) * 16) = v[j];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (*(volatile int *)abort_flag != 0) {
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
-      if (!bar_wait(&loaded[s], (c >> 1) & 1)) {
-        atomicExch(abort_flag, 1);
-      } else {
-        copy_pending = -1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-        for (int ks = 0; ks < kKC / 16; ks++) {
-          const uint64_t da = smem_desc(su32(sa) + 2 * ks * kLboA, kLboA, 128);
-          const uint64_t db = smem_desc(su32(sb) + 2 * ks * lbo_b, lbo_b, 128);
-          const unsigned acc = (c > 0 || ks > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(da), "l"(db), "r"(idesc), "r"(acc)
-              : "memory");
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         su32(&done[s]))
-                     : "memory");
-        issued = c + 1;
-      }
-    }
-  }
-  // a weight copy still in flight lands before the block's shared memory is released
-  if (tid == 0 && copy_pending >= 0) bar_wait(&loaded[copy_pending & 1], (copy_pending >> 1) & 1);
-  // every thread learns the count of committed chunks from thread 0
-  __syncthreads();
-  if (tid == 0) tslot[1] = (unsigned)issued;
-  __syncthreads();
-  issued = (int)tslot[1];
-  if (*(volatile int *)abort_flag != 0) ok = false;
-  // the last commit covers every MMA issued before it
-  if (issued > 0 && !bar_wait(&done[(issued - 1) & 1], ((issued - 1) >> 1) & 1)) ok = false;
-  ok = __syncthreads_and(ok) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its voxels), columns of its half
-  const int q = warp & 3, chalf = warp >> 2;
-  const int64_t pe = p0 + q * 32 + lane;
-  const int cols_half = nt_n / 2;  // a multiple of 8
-  for (int c0 = chalf * cols_half; c0 < (chalf + 1) * cols_half; c0 += 8) {
-    uint32_t r[8];
-    const unsigned ta = tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(ta));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (pe < nv) {
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        const int co = nt * nt_n + c0 + j;
-        if (co >= cout) continue;
-        if constexpr (BWD) {
-          static_cast<float *>(yout)[(int64_t)co * nv + pe] = ok ? __uint_as_float(r[j]) : __uint_as_float(0x7FC00000u);
-        } else {
-          float v = __uint_as_float(r[j]) + (bias ? __ldg(bias + co) : 0.f);
-          if (relu) v = fmaxf(v, 0.f);
-          const uint16_t o = ok ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : (uint16_t)0x7FC0;
-          static_cast<uint16_t *>(yout)[(int64_t)co * nv + pe] = o;
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
 }  // namespace
@@ -552,47 +333,336 @@ cudaError_t conv3d_backward_weight_tc(const float *dy, const uint16_t *x, int ci
 
 namespace {
 
-// the GEMM over n_out output rows (tiles of up to 256) with reduce channels cpa per tap;
-// src: the channels-last source the caller's `prepare` fills (nv x cpa BF16)
-template <bool BWD, class Prepare>
-cudaError_t run_igemm(const uint16_t *w, const float *b, int n_out, int n_red, int cgrp, int cpa, int D, int H, int W,
-                      int relu, void *y, cudaStream_t s, Prepare prepare) {
-  const cudaError_t attr =
-      cudaFuncSetAttribute(igemm_kernel<BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-  if (attr != cudaSuccess) return attr;
-  const int64_t kpad = ((int64_t)27 * cpa + kKC - 1) / kKC * kKC;
+// ---- tile form of the forward and backward-data convolutions. The source is a
+// channel-group-major copy src[g][z][y][x][8] (G groups of 8 channels, zero past the real
+// ones). A block owns an output tile of 8 (x) x 16 (y) voxels of one plane (MMA M = 128,
+// m = 8 y + x) and up to 256 GEMM output channels (N). Per pass of Gp groups one TMA box
+// (8 channels, 10 x 18 x 3 voxels, Gp groups) brings the tile with its halo into shared
+// memory as [g][z][y][x][8], zero outside the grid. The A operand of tap t and group pair
+// (2j, 2j + 1) is then a view of that box: core matrix y = the 8 x-voxels of row y (16 bytes
+// each, contiguous), start at the tap's shifted voxel, SBO = one staged row (160 bytes),
+// LBO = one staged group (8640 bytes). No thread gathers anything.
+// Weights stream per (pass, tap) chunk (N x Gp x 8 BF16, K-major, packed once per call by
+// tile_pack_kernel) through a ring of 4 buffers by bulk copies. One thread drives the copies
+// and the MMAs; all threads run the epilogue.
+constexpr int kTX = 8, kTY = 16;                // output tile (x, y)
+constexpr int kBX = kTX + 2, kBY = kTY + 2;     // staged box with the halo
+constexpr int kGroupBytes = kBX * kBY * 3 * 16;  // one staged group: 8640 bytes
+constexpr int kRowBytes = kBX * 16;             // one staged row: 160 bytes
+constexpr int kRingB = 4;                       // weight chunks in flight
+constexpr int kTileThreads = 128;
+
+// src[g][p][e] = x[8 g + e][p] (zero for channels >= cin)
+__global__ void to_group_major(const uint16_t *__restrict__ x, int64_t nv, int cin, int G, uint16_t *__restrict__ src) {
+  const int64_t total = nv * G;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i % nv;
+    const int g = (int)(i / nv);
+    uint32_t v[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int e = 0; e < 8; e++)
+      if (8 * g + e < cin) v[e >> 1] |= (uint32_t)__ldg(x + (int64_t)(8 * g + e) * nv + p) << (16 * (e & 1));
+    *reinterpret_cast<uint4 *>(src + ((int64_t)g * nv + p) * 8) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// src[g][p][e] = part s of dy[co][p] for channel 8 g + e = s cop + co (three BF16 parts,
+// as split_channels_last), zero for co >= cout and for channels past 3 cop
+__global__ void split_group_major(const float *__restrict__ dy, int64_t nv, int cout, int cop, int G,
+                                  uint16_t *__restrict__ src) {
+  const int64_t total = nv * G;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i % nv;
+    const int g = (int)(i / nv);
+    uint32_t v[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      const int c = 8 * g + e, part = c / cop, co = c % cop;
+      if (part >= 3 || co >= cout) continue;
+      float r = __ldg(dy + (int64_t)co * nv + p);
+      uint16_t h = 0;
+      for (int q = 0; q <= part; q++) {
+        h = __bfloat16_as_ushort(__float2bfloat16_rn(r));
+        r -= __uint_as_float((uint32_t)h << 16);
+      }
+      v[e >> 1] |= (uint32_t)h << (16 * (e & 1));
+    }
+    *reinterpret_cast<uint4 *>(src + ((int64_t)g * nv + p) * 8) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// weight chunks: for N tile nt, pass ps, tap t: N x (Gp x 8) K-major, core (kg, ng) at
+// kg * (N / 8) * 128 + ng * 128. Source channel c = 8 (ps Gp + kg) + kk; forward: w[n][c][t];
+// backward: c = s cop + co, w[co][n][t]
+__global__ void tile_pack_kernel(const uint16_t *__restrict__ w, int n_rows, int n_red, int cop, bool bwd, int nt_n,
+                                 int gp, int npass, int ntiles, uint16_t *__restrict__ out) {
+  const int64_t chunk = (int64_t)nt_n * gp * 8;
+  const int64_t total = (int64_t)ntiles * npass * 27 * chunk;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(i % 8), row = (int)(i / 8 % 8);
+    const int64_t r = i / 64;
+    const int ng = (int)(r % (nt_n / 8)), kg = (int)(r / (nt_n / 8) % gp);
+    const int64_t q = r / (nt_n / 8) / gp;  // (tile, pass, tap)
+    const int t = (int)(q % 27), ps = (int)(q / 27 % npass), nt = (int)(q / 27 / npass);
+    const int n = nt * nt_n + ng * 8 + row;
+    const int c = 8 * (ps * gp + kg) + kk;
+    uint16_t v = 0;
+    if (n < n_rows) {
+      if (!bwd) {
+        if (c < n_red) v = w[((int64_t)n * n_red + c) * 27 + t];
+      } else {
+        const int part = c / cop, co = c % cop;
+        if (part < 3 && co < n_red) v = w[((int64_t)co * n_rows + n) * 27 + t];
+      }
+    }
+    out[i] = v;
+  }
+}
+
+__device__ __forceinline__ void tma_box5(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3, int c4,
+                                         uint64_t *b) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(b))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *b) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(b))
+               : "memory");
+}
+
+template <bool BWD>
+__global__ void __launch_bounds__(kTileThreads)
+    tile_conv_kernel(const __grid_constant__ CUtensorMap tm, const uint16_t *__restrict__ wpack,
+                     const float *__restrict__ bias, int n_out, int nt_n, int tmem_cols, int gp, int npass, int D, int H,
+                     int W, int relu, void *__restrict__ yout) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int a_bytes = kGroupBytes * gp;
+  const int b_bytes = nt_n * gp * 16;  // one chunk
+  unsigned char *sa = sm;
+  unsigned char *sb = sm + (a_bytes + 127) / 128 * 128;
+  uint64_t *loaded = reinterpret_cast<uint64_t *>(sb + kRingB * b_bytes);  // [kRingB]
+  uint64_t *done = loaded + kRingB;                                        // [kRingB]
+  uint64_t *a_full = done + kRingB;
+  unsigned *tslot = reinterpret_cast<unsigned *>(a_full + 1);
+  int *okslot = reinterpret_cast<int *>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntx = (W + kTX - 1) / kTX;
+  const int x0 = (blockIdx.x % ntx) * kTX, y0 = (blockIdx.x / ntx) * kTY, z0 = blockIdx.y;
+  const int nt = blockIdx.z;
+  const unsigned lbo_b = (unsigned)(nt_n / 8) * 128u;
+  const int nch = npass * 27;
+  const uint16_t *wt = wpack + (int64_t)nt * nch * nt_n * gp * 8;
+
+  if (tid == 0) {
+    for (int i = 0; i < kRingB; i++) {
+      bar_init(&loaded[i]);
+      bar_init(&done[i]);
+    }
+    bar_init(a_full);
+    *okslot = 1;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tslot;
+
+  if (tid == 0) {
+    const uint32_t idesc = instr_desc(nt_n);
+    bool ok = true;
+    int copies = 0, committed = 0;  // weight chunks issued / chunks whose MMAs are committed
+    int a_pending = -1;  // the pass whose box copy has not been waited for
+    auto chunk_src = [&](int c) { return wt + (int64_t)c * nt_n * gp * 8; };
+    for (; copies < kRingB && copies < nch; copies++) bulk_copy(sb + copies * b_bytes, chunk_src(copies), b_bytes, &loaded[copies]);
+    for (int c = 0; c < nch && ok; c++) {
+      const int ps = c / 27, t = c % 27, s = c % kRingB;
+      if (t == 0) {
+        // a new pass: the previous pass's MMAs read the box, so they finish first
+        if (c > 0 && !bar_wait(&done[(c - 1) % kRingB], ((c - 1) / kRingB) & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(a_full)), "r"(a_bytes)
+                     : "memory");
+        tma_box5(sa, &tm, 0, x0 - 1, y0 - 1, z0 - 1, ps * gp, a_full);
+        a_pending = ps;
+        if (!bar_wait(a_full, ps & 1)) {
+          ok = false;
+          break;
+        }
+        a_pending = -1;
+      }
+      if (!bar_wait(&loaded[s], (c / kRingB) & 1)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // the tap's shift (mirrored for the backward pass), as a staged voxel offset
+      const int dx = t % 3 - 1, dy = t / 3 % 3 - 1, dz = t / 9 - 1;
+      const int sx = BWD ? 1 - dx : 1 + dx, sy = BWD ? 1 - dy : 1 + dy, sz = BWD ? 1 - dz : 1 + dz;
+      const unsigned a0 = su32(sa) + (unsigned)(((sz * kBY) + sy) * kBX + sx) * 16u;
+      const unsigned b0 = su32(sb + s * b_bytes);
+      for (int j = 0; j < gp / 2; j++) {
+        const uint64_t da = smem_desc(a0 + 2 * j * kGroupBytes, kGroupBytes, kRowBytes);
+        const uint64_t db = smem_desc(b0 + 2 * j * lbo_b, lbo_b, 128);
+        const unsigned acc = (c > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&done[s]))
+                   : "memory");
+      committed = c + 1;
+      // refill the buffer of chunk c - 1 (its MMAs ran before this chunk's) with chunk c + 3
+      if (c >= 1 && copies < nch) {
+        const int sp = (c - 1) % kRingB;
+        if (!bar_wait(&done[sp], ((c - 1) / kRingB) & 1)) {
+          ok = false;
+          break;
+        }
+        bulk_copy(sb + sp * b_bytes, chunk_src(copies), b_bytes, &loaded[sp]);
+        copies++;
+      }
+    }
+    // copies still in flight land before the shared memory is released
+    if (a_pending >= 0) bar_wait(a_full, a_pending & 1);
+    for (int c = committed; c < copies; c++) bar_wait(&loaded[c % kRingB], (c / kRingB) & 1);
+    if (committed > 0 && !bar_wait(&done[(committed - 1) % kRingB], ((committed - 1) / kRingB) & 1)) ok = false;
+    if (committed < nch) ok = false;
+    *okslot = ok ? 1 : 0;
+  }
+  __syncthreads();
+  const bool ok = *(volatile int *)okslot != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // epilogue: warp q reads TMEM lanes 32 q .. 32 q + 31 (tile rows 4 q .. 4 q + 3)
+  const int m = warp * 32 + lane;
+  const int ox = x0 + (m & 7), oy = y0 + (m >> 3);
+  const bool in = ox < W && oy < H;
   const int64_t nv = (int64_t)D * H * W;
-  const int64_t nblk = (nv + kM - 1) / kM;
-  if (nblk > 0x7fffffff || kpad / kKC > 0x7fffffff) return cudaErrorInvalidValue;
-  const int nchunk = (int)(kpad / kKC);
-  const int n16 = (n_out + 15) / 16 * 16;
+  const int64_t pe = ((int64_t)z0 * H + oy) * W + ox;
+  for (int c0 = 0; c0 < nt_n; c0 += 8) {
+    uint32_t r[8];
+    const unsigned ta = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (in) {
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int co = nt * nt_n + c0 + j;
+        if (co >= n_out) continue;
+        if constexpr (BWD) {
+          static_cast<float *>(yout)[(int64_t)co * nv + pe] = ok ? __uint_as_float(r[j]) : __uint_as_float(0x7FC00000u);
+        } else {
+          float v = __uint_as_float(r[j]) + (bias ? __ldg(bias + co) : 0.f);
+          if (relu) v = fmaxf(v, 0.f);
+          static_cast<uint16_t *>(yout)[(int64_t)co * nv + pe] =
+              ok ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : (uint16_t)0x7FC0;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static const EncodeTiled fn = []() -> EncodeTiled {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// the tile form over a group-major source of G groups (G a multiple of 4) that `prepare`
+// fills; n_rows GEMM output channels, n_red real source channels (forward: cin; backward:
+// cout, with cop = the part stride)
+template <bool BWD, class Prepare>
+cudaError_t run_tile(const uint16_t *w, const float *b, int n_rows, int n_red, int cop, int G, int D, int H, int W,
+                     int relu, void *y, cudaStream_t s, Prepare prepare) {
+  const EncodeTiled enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const int n16 = (n_rows + 15) / 16 * 16;
   const int nt_n = n16 < kMaxN ? n16 : kMaxN;
-  const int ntiles = (n_out + nt_n - 1) / nt_n;
+  const int ntiles = (n_rows + nt_n - 1) / nt_n;
   int tmem_cols = 32;
   while (tmem_cols < nt_n) tmem_cols *= 2;
-  // shared memory per block: the buffers, raised where needed so that the blocks one SM
-  // can hold never ask for more than its 512 TMEM columns (an allocation would wait)
+  // groups per pass: the largest of 12, 8, 4 that divides G and fits shared memory
+  int gp = 0, smem = 0;
+  for (int cand : {12, 8, 4}) {
+    if (G % cand) continue;
+    const int need = (kGroupBytes * cand + 127) / 128 * 128 + kRingB * nt_n * cand * 16 + 2 * kRingB * 8 + 32;
+    if (need <= 200 * 1024) {
+      gp = cand;
+      smem = need;
+      break;
+    }
+  }
+  if (gp == 0) return cudaErrorInvalidValue;
+  const int npass = G / gp;
   const int max_blocks = 512 / tmem_cols;
-  int smem = kOffB + 2 * nt_n * kKC * 2 + 64;
   const int floor_smem = kSmPerSM / (max_blocks + 1) - 1024 + 16;
   if (smem < floor_smem) smem = floor_smem;
-  if (smem > kSmemMax) smem = kSmemMax;
-  const size_t pack_elems = (size_t)ntiles * nchunk * nt_n * kKC;
-  uint16_t *wp = nullptr, *src = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&wp), pack_elems * sizeof(uint16_t), s);
+  const int64_t nv = (int64_t)D * H * W;
+  const int64_t tiles_xy = (int64_t)((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY);
+  if (tiles_xy > 0x7fffffff || D > 65535 || ntiles > 65535) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(tile_conv_kernel<BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaMallocAsync(reinterpret_cast<void **>(&src), (size_t)nv * cpa * sizeof(uint16_t), s);
+  const size_t pack_elems = (size_t)ntiles * npass * 27 * nt_n * gp * 8;
+  uint16_t *wp = nullptr, *src = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&wp), pack_elems * sizeof(uint16_t), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMallocAsync(reinterpret_cast<void **>(&src), (size_t)G * nv * 8 * sizeof(uint16_t), s);
   if (e != cudaSuccess) {
     cudaFreeAsync(wp, s);
     return e;
   }
+  // tensor map of src as (8 channels, W, H, D, G) BF16; boxes (8, 10, 18, 3, gp), zero outside
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)G};
+  const cuuint64_t pitch[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)nv * 16};
+  const cuuint32_t box[5] = {8, kBX, kBY, 3, (cuuint32_t)gp};
+  const cuuint32_t step[5] = {1, 1, 1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, src, dims, pitch, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS) {
+    cudaFreeAsync(src, s);
+    cudaFreeAsync(wp, s);
+    return cudaErrorInvalidValue;
+  }
   const int64_t pblocks = ((int64_t)pack_elems + 255) / 256;
-  pack_kernel<<<(unsigned)(pblocks < 4096 ? pblocks : 4096), 256, 0, s>>>(w, n_out, n_red, cgrp, cpa, BWD, nt_n,
-                                                                           nchunk, ntiles, wp);
-  const int64_t xblocks = (nv * (cpa / 8) + 255) / 256;
+  tile_pack_kernel<<<(unsigned)(pblocks < 4096 ? pblocks : 4096), 256, 0, s>>>(w, n_rows, n_red, cop, BWD, nt_n, gp,
+                                                                               npass, ntiles, wp);
+  const int64_t xblocks = (nv * G + 255) / 256;
   prepare(src, (unsigned)(xblocks < 65536 ? xblocks : 65536));
-  igemm_kernel<BWD><<<dim3((unsigned)nblk, (unsigned)ntiles), kThreads, smem, s>>>(
-      src, wp, b, n_out, cpa, nt_n, tmem_cols, nchunk, D, H, W, relu, y);
+  tile_conv_kernel<BWD><<<dim3((unsigned)tiles_xy, (unsigned)D, (unsigned)ntiles), kTileThreads, smem, s>>>(
+      tm, wp, b, n_rows, nt_n, tmem_cols, gp, npass, D, H, W, relu, y);
   e = cudaGetLastError();
   const cudaError_t f1 = cudaFreeAsync(src, s), f2 = cudaFreeAsync(wp, s);
   return e != cudaSuccess ? e : (f1 != cudaSuccess ? f1 : f2);
@@ -600,21 +670,23 @@ cudaError_t run_igemm(const uint16_t *w, const float *b, int n_out, int n_red, i
 
 }  // namespace
 
+
 cudaError_t conv3d_forward_tc(const uint16_t *x, const uint16_t *w, const float *b, int cin, int cout, int D, int H,
                               int W, int relu, uint16_t *y, cudaStream_t s) {
-  const int cp = (cin + 7) / 8 * 8;
+  const int G = (cin + 31) / 32 * 4;  // groups of 8 channels, a multiple of 4
   const int64_t nv = (int64_t)D * H * W;
-  return run_igemm<false>(w, b, cout, cin, cp, cp, D, H, W, relu, y, s, [&](uint16_t *src, unsigned blocks) {
-    to_channels_last<<<blocks, 256, 0, s>>>(x, nv, cin, cp, src);
+  return run_tile<false>(w, b, cout, cin, 0, G, D, H, W, relu, y, s, [&](uint16_t *src, unsigned blocks) {
+    to_group_major<<<blocks, 256, 0, s>>>(x, nv, cin, G, src);
   });
 }
 
 cudaError_t conv3d_backward_data_tc(const float *dy, const uint16_t *w, int cin, int cout, int D, int H, int W,
                                     float *dx, cudaStream_t s) {
   const int cop = (cout + 7) / 8 * 8;
+  const int G = (3 * cop / 8 + 3) / 4 * 4;
   const int64_t nv = (int64_t)D * H * W;
-  return run_igemm<true>(w, nullptr, cin, cout, cop, 3 * cop, D, H, W, 0, dx, s, [&](uint16_t *src, unsigned blocks) {
-    split_channels_last<<<blocks, 256, 0, s>>>(dy, nv, cout, cop, src);
+  return run_tile<true>(w, nullptr, cin, cout, cop, G, D, H, W, 0, dx, s, [&](uint16_t *src, unsigned blocks) {
+    split_group_major<<<blocks, 256, 0, s>>>(dy, nv, cout, cop, G, src);
   });
 }
 
