@@ -117,7 +117,9 @@ def test_null_context_is_rejected_without_touching_the_gpu():
     assert lib.fwi_nn_conv3d_backward_data(one, one, 1, 1, 0, 2, 2, one, nul) == inval
     assert lib.fwi_nn_conv3d_backward_weight(one, one, 1, 1, 2, 2, 2, one, nul, nul, nul) == inval
     assert lib.fwi_nn_conv3d_backward_weight_work(0, 1, 2, 2, 2) == 0
-    assert lib.fwi_nn_conv3d_backward_weight_work(3, 4, 2, 2, 2) == 1 * 4 * 3 * 28
+    # one 2048-voxel slice x 16 output-channel columns x (27 x 8 + 1 rows, padded to 256)
+    assert lib.fwi_nn_conv3d_backward_weight_work(3, 4, 2, 2, 2) == 1 * 16 * 256
+    assert lib.fwi_nn_conv3d_backward_weight_work(3, 4, 20, 20, 24) == 5 * 16 * 256
     assert lib.fwi_nn_relu_backward(one, one, 0, one, nul) == inval
     assert lib.fwi_nn_mse(one, one, 10, one, nul, one, nul) == inval
     assert lib.fwi_nn_adam(one, nul, one, one, one, 10, 1e-3, 0.9, 0.999, 1e-8, 0, nul) == inval
