@@ -337,7 +337,7 @@ namespace {
 // channel-group-major copy src[g][z][y][x][8] (G groups of 8 channels, zero past the real
 // ones). A block owns an output tile of 8 (x) x 16 (y) voxels of one plane (MMA M = 128,
 // m = 8 y + x) and up to 256 GEMM output channels (N). Per pass of Gp groups one TMA box
-// (8 channels, 10 x 18 x 3 voxels, Gp groups) brings the tile with its halo into shared
+// (10 voxels x 8 channels as one 160-byte row, 18 rows, 3 planes, Gp groups) brings the tile with its halo into shared
 // memory as [g][z][y][x][8], zero outside the grid. The A operand of tap t and group pair
 // (2j, 2j + 1) is then a view of that box: core matrix y = the 8 x-voxels of row y (16 bytes
 // each, contiguous), start at the tap's shifted voxel, SBO = one staged row (160 bytes),
@@ -419,12 +419,13 @@ __global__ void tile_pack_kernel(const uint16_t *__restrict__ w, int n_rows, int
   }
 }
 
-__device__ __forceinline__ void tma_box5(void *dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3, int c4,
-                                         uint64_t *b) {
+// the halo box of a tile: x and the 8 channels of a group form one row of 80 elements (the
+// inner coordinate 8 (x0 - 1) is a multiple of 16 bytes), then y, z and the groups
+__device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *tm, int x0, int y0, int z0, int g0, uint64_t *b) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-      "%6}], [%7];" ::"r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(b))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(8 * (x0 - 1)), "r"(y0 - 1), "r"(z0 - 1), "r"(g0), "r"(su32(b))
       : "memory");
 }
 __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, uint64_t *b) {
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(kTileThreads)
         }
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(a_full)), "r"(a_bytes)
                      : "memory");
-        tma_box5(sa, &tm, 0, x0 - 1, y0 - 1, z0 - 1, ps * gp, a_full);
+        tma_box(sa, &tm, x0, y0, z0, ps * gp, a_full);
         a_pending = ps;
         if (!bar_wait(a_full, ps & 1)) {
           ok = false;
@@ -642,14 +643,15 @@ cudaError_t run_tile(const uint16_t *w, const float *b, int n_rows, int n_red, i
     cudaFreeAsync(wp, s);
     return e;
   }
-  // tensor map of src as (8 channels, W, H, D, G) BF16; boxes (8, 10, 18, 3, gp), zero outside
+  // tensor map of src as (x and 8 channels: 8 W, H, D, G) BF16; boxes (80, 18, 3, gp), zero
+  // outside the grid
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));
-  const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)G};
-  const cuuint64_t pitch[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)nv * 16};
-  const cuuint32_t box[5] = {8, kBX, kBY, 3, (cuuint32_t)gp};
-  const cuuint32_t step[5] = {1, 1, 1, 1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, src, dims, pitch, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const cuuint64_t dims[4] = {(cuuint64_t)W * 8, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)G};
+  const cuuint64_t pitch[3] = {(cuuint64_t)W * 16, (cuuint64_t)W * H * 16, (cuuint64_t)nv * 16};
+  const cuuint32_t box[4] = {kBX * 8, kBY, 3, (cuuint32_t)gp};
+  const cuuint32_t step[4] = {1, 1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, src, dims, pitch, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
       CUDA_SUCCESS) {
     cudaFreeAsync(src, s);
