@@ -498,6 +498,9 @@ __device__ __forceinline__ void face_write(const Geo &g, const StageArgs &a, con
   }
 }
 
+#ifndef FWI_PML_STAGE4_MINB
+#define FWI_PML_STAGE4_MINB 7  // stage 4 reads three more step-start rows: 72 registers, no spills
+#endif
 #ifndef FWI_PML_SPLIT_MINB
 #define FWI_PML_SPLIT_MINB 8
 #endif
@@ -528,7 +531,7 @@ __device__ __forceinline__ void pml_task(const Geo &g, const StageArgs &a, int I
 }
 
 template <bool ADJ, int MODE, int PART>
-__global__ void __launch_bounds__(kBX *kBY, PART == 0 ? FWI_PML_MINB : FWI_PML_SPLIT_MINB)
+__global__ void __launch_bounds__(kBX *kBY, MODE == 3 ? FWI_PML_STAGE4_MINB : (PART == 0 ? FWI_PML_MINB : FWI_PML_SPLIT_MINB))
     pml_kernel(Geo g, StageArgs a0, Region r) {
   const int nbs = (r.tasks_before[r.nbox] + kBY - 1) / kBY;  // blocks per shot
   const StageArgs a = shot_args(a0, blockIdx.x / nbs);
