@@ -137,7 +137,9 @@ fwi_status fwi_set_receivers(fwi_ctx *ctx, int nrec, const int *node_ijk);
  * displacements traces[s][n][r][c] = u_c(x_r, t_n), n = 0..nsteps, FP32
  * (host or device, caller-owned, nshots*(nsteps+1)*nrec*3 floats).
  * Errors: FWI_E_STATE (no material / sources / receivers), FWI_E_INVAL,
- * FWI_E_NONFINITE, FWI_E_CUDA. */
+ * FWI_E_NONFINITE, FWI_E_TIMEOUT (a bounded device wait gave up: a grid barrier of the
+ * persistent sweep, or a plane copy of the interior kernel; the context stays usable),
+ * FWI_E_BOUNDS (bounds-checked build only), FWI_E_CUDA. */
 fwi_status fwi_forward(fwi_ctx *ctx, int shot0, int nshots, float *traces, int on_device);
 
 /* Misfit (7) without regularisation, summed over the shots, with the trapezoid
