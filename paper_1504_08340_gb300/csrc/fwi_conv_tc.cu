@@ -50,7 +50,8 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsig
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B
-// (bits 7-9, 10-12 = 1), both K-major, N / 8 at bit 17, M / 16 at bit 24
+// (bits 7-9, 10-12 = 1), N / 8 at bit 17, M / 16 at bit 24; both operands K-major (a caller
+// sets bit 15 for an MN-major A)
 __host__ __device__ constexpr uint32_t instr_desc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
 }
@@ -89,10 +90,6 @@ __global__ void to_channels_last(const uint16_t *__restrict__ x, int64_t nv, int
     *reinterpret_cast<uint4 *>(xcl + p * cp + c0) = make_uint4(v[0], v[1], v[2], v[3]);
   }
 }
-
-}  // namespace
-
-namespace {
 
 // ---- weight gradient: dW[m][co] = sum_p A[p][m] dy[co][p], m = t Cp + ci (tap t, input
 // channel ci) and one more row m = 27 Cp of ones (the bias gradient), over a slice of
