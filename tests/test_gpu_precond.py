@@ -98,8 +98,9 @@ def _bwd_data_tol(cout):
     """Relative L2 bound of the backward-data sums: K = 27 x 3 x ceil(cout / 8) x 8 exact
     products (three BF16 parts of each FP32 gradient value, BF16 weights) accumulated in
     FP32 on the tensor cores. A random walk of round-to-nearest adds would give about
-    2^-24 sqrt(K); the MMA aligns and truncates its partial sums, so the errors share a
-    sign and the bound takes four times that: 2^-22 sqrt(K)."""
+    2^-24 sqrt(K). The tensor cores' internal accumulation is not a sequence of
+    round-to-nearest adds (it measured about twice that estimate at K = 9072), so the bound
+    takes four times it: 2^-22 sqrt(K)."""
     k = 27 * 3 * ((cout + 7) // 8 * 8)
     return 2.0 ** -22 * np.sqrt(k)
 
